@@ -1,0 +1,332 @@
+"""Benchmark: MAR-DEAM iterations/s on the full-size 3D helical workload.
+
+Workload: 512x512x64 voxels (0.98 x 0.98 x 0.75 mm) per basis component, 16-row
+x 816-channel curved detector, 1160 views/rotation x 5 rotations (5800 views),
+pitch 0.6, two spectra x 120 one-keV bins, bilateral stainless-steel hip inserts
+(dense metal trace), Poisson I0 = 1e5 plus Gaussian electronic noise sigma = 5.
+Synthetic seeded data (no scanner data offline).
+
+One step = one MAR-DEAM iteration: forward projection + fused spectral sums,
+metal substitution, p-step ratio and objective; objective reduction; gather
+backprojection fused with the c-step.  value = iterations/s with the data
+resident in HBM; e2e = the same through the C ABI with host buffers (data,
+mask and image copied in, image and objective copied out, every step).
+
+--impl reference times the FP64 CPU oracle (the reference arm of this build) on
+a bounded view sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "DEAM iterations/s"
+UNIT = "it/s"
+WORKLOAD = ("3D helical MAR-DEAM, 512x512x64 voxels x 2 components (0.98x0.98x0.75 mm), "
+            "16x816 curved detector, 5800 views (1160/rot x 5, pitch 0.6), 2 spectra x 120 bins, "
+            "bilateral steel hips, I0=1e5 + sigma 5")
+FP32_LANES_PER_SM = 128
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    smax.append(float(p[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, p[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+            os.unlink(self.path)
+        except OSError:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def build_workload(name, device):
+    import torch
+
+    import synth
+    case = synth.make_case(name)
+    d, metal = synth.measure(case, device=device, seed=1)
+    truth, M = synth.voxelize(case, device=device)
+    mask = (metal >= case.metal_threshold).to(torch.uint8)
+    c0 = synth.initial_image(case, truth).to(device)
+    return case, d, mask, c0
+
+
+def dist_init(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if (args.impl != "reference" and torch.cuda.is_available()) else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def cpu_oracle_rate(case, d, mask, c0, seconds=15.0, views=None):
+    """Oracle iterations/s measured on a bounded view sample (the oracle's rays
+    restricted to a contiguous view range; the c-step runs over all voxels).
+    Returns (value, sample description, threads, seconds spent)."""
+    import numpy as np
+
+    import oracle
+    O = oracle.from_case(case)
+    dn = d.detach().cpu().double().numpy()
+    mn = mask.detach().cpu().numpy()
+    cn = c0.detach().cpu().double().numpy()
+    V = case.geo.n_views
+    Z = O.normaliser() if case.geo.n_rays < 2e6 else 1.0   # Z only scales the update; not timed
+    mid = V // 2
+    if views is None:
+        nv = max(1, V // 400)
+        t = time.perf_counter()
+        O.iterate(cn, dn, mn, n_iter=1, Z=Z, v0=mid, v1=mid + nv)
+        dt = time.perf_counter() - t
+        views = int(max(1, min(V, nv * seconds / max(dt, 1e-3))))
+    v0 = max(0, mid - views // 2)
+    v1 = min(V, v0 + views)
+    t = time.perf_counter()
+    O.iterate(cn, dn, mn, n_iter=1, Z=Z, v0=v0, v1=v1)
+    dt = time.perf_counter() - t
+    frac = (v1 - v0) / V
+    rate = frac / dt   # full iterations per second, extrapolated linearly in views
+    desc = (f"one oracle iteration over views [{v0},{v1}) = {v1 - v0}/{V} views "
+            f"({100 * frac:.2f}%) plus the full c-step; {dt:.2f} s; scaled by views")
+    return rate, desc, oracle.lib().or_num_threads(), dt
+
+
+def run_reference(args):
+    import torch
+    world, rank, local, pg = dist_init(args)
+    if rank != 0:
+        return 0
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    case, d, mask, c0 = build_workload(args.config, dev)
+    import oracle
+    oracle.build()
+    budget = max(5.0, 120.0 / max(1, args.steps + args.warmup))
+    rate, desc, cores, _ = cpu_oracle_rate(case, d, mask, c0, seconds=budget)
+    # fixed sample size from the calibration, then W warm-up and K timed steps
+    views = max(1, int(round(rate * budget * case.geo.n_views)))
+    times = []
+    for i in range(args.warmup + args.steps):
+        r, desc, cores, dt = cpu_oracle_rate(case, d, mask, c0, views=views)
+        if i >= args.warmup:
+            times.append(dt / ((views) / case.geo.n_views))
+    sec_per_it = sum(times) / len(times)
+    value = 1.0 / sec_per_it
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec_per_it,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "case": args.config},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    import paper_2202_00116_gb300 as pkg
+    from paper_2202_00116_gb300 import build
+    world, rank, local, pg = dist_init(args)
+    if not torch.cuda.is_available():
+        print(json.dumps({"metric": METRIC, "error": "no CUDA device"}))
+        return 1
+    torch.cuda.set_device(local)
+    build.build()
+    dev = torch.device("cuda", local)
+    case, d, mask, c0 = build_workload(args.config, dev)
+    geo = case.geo
+    gpu = pkg.from_case(case)
+    gpu.set_data(d)
+    gpu.set_metal_mask(mask, "ray")
+    samples = gpu.count_samples()
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize(dev)
+
+    # ---- device-resident timing ----
+    c = c0.clone()
+    gpu.iterate(c, args.warmup)
+    barrier()
+    gpu.profile(True)
+    gpu.kernel_times(reset=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hist = gpu.iterate(c, args.steps)
+        e1.record(stream)
+        barrier()
+    gpu.profile(False)
+    ms = e0.elapsed_time(e1)
+    kms, kn = gpu.kernel_times(reset=True)
+    if pg is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * args.steps / (ms / 1e3)
+
+    # ---- end to end through the C ABI with host buffers ----
+    d_h = d.cpu().pin_memory()
+    m_h = mask.cpu().pin_memory()
+    c_h = c0.cpu().pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        gpu.set_data(d_h)
+        gpu.set_metal_mask(m_h, "ray")
+        gpu.iterate(c_h, 1)      # copies c in, iterates, copies c and F out (synchronous)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if pg is not None:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_val = world * e2e_steps / e2e_s
+    h2d = d_h.numel() * 4 + m_h.numel() + c_h.numel() * 4
+    d2h = c_h.numel() * 4 + 8
+
+    # ---- roofline of the dominant kernel ----
+    stages = ["layout", "forward", "reduce", "backproject"]
+    avg = {s: kms[i] / max(kn[i], 1) * (2 if s == "layout" else 1) for i, s in enumerate(stages)}
+    dom = max(["forward", "backproject"], key=lambda s: avg[s])
+    peaks = _peaks()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12   # TFLOP/s, FMA = 2 flops
+    # algorithmic flops per Joseph sample: forward = 6 two-point interpolations of
+    # 2 components (12 flops); backprojection = 4 taps x 4 accumulators FMA (32
+    # flops) + 4 tap weights (4 flops)
+    flops_per_sample = {"forward": 12.0, "backproject": 36.0}[dom]
+    achieved = flops_per_sample * samples / (avg[dom] / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": {"forward": "fwd_kernel<FWD_DEAM>", "backproject": "bwd_kernel<1>"}[dom],
+                "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                "peak_source": f"FP32 lanes 152 SMs x 128 x 2 flops x {sm_max:.0f} MHz (derived)",
+                "traffic": None,
+                "ms_per_launch": avg[dom],
+                "hbm_compulsory_GBps": None}
+    nvox, nrays = geo.n_voxels, geo.n_rays
+    comp_bytes = {"forward": 16 * nvox + 8 * nrays + nrays + 16 * nrays,
+                  "backproject": 16 * nrays + 16 * nvox}[dom]
+    hbm = peaks.get("hbm_gbs", 6780.4)
+    roofline["hbm_compulsory_GBps"] = comp_bytes / (avg[dom] / 1e3) / 1e9
+    roofline["hbm_frac"] = roofline["hbm_compulsory_GBps"] / hbm
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded phantom, analytic polyenergetic projections, Poisson + Gaussian noise)",
+            "config": {"workload": WORKLOAD, "case": args.config, "parallelism": f"replicas x{world}",
+                       "l2": "working set larger than L2 (payload 1.2 GB + data 0.6 GB per iteration)"},
+            "ray_samples_per_projection": samples,
+            "ray_samples_per_s": samples * value,
+            "stage_ms": {s: avg[s] for s in stages},
+            "objective_first_last": [float(hist[0]), float(hist[-1])],
+            "gpu_launches": int(sum(kn)),
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "roofline": roofline,
+            "clocks": clk.summary()}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, desc, cores, _ = cpu_oracle_rate(case, d, mask, c0, seconds=args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    gpu.close()
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--config", default="c2")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

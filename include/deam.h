@@ -1,0 +1,188 @@
+/*
+ * deam.h -- C ABI of the GB300 (sm_103a) MAR-DEAM library (libdeam.so).
+ *
+ * MAR-DEAM (Ge et al., "A Metal Artifact Reduction Scheme For Accurate Iterative
+ * Dual-Energy CT Algorithms", arXiv 2202.00116) reconstructs two basis-component
+ * images c_1, c_2 from low- and high-kVp transmission data d_L, d_H by dual-energy
+ * alternating minimisation (DEAM) of the I-divergence (Sec. 2.3, Eq. 5) between the
+ * data and the polyenergetic forward model
+ *     g_j(y:c) = sum_E I0_j(y,E) exp(-sum_x h(x,y) sum_i mu_i(E) c_i(x))   (Eq. 8),
+ * where every ray on the metal trace T(y) = sum_x h(x,y) M(x) >= t has its data
+ * replaced by the current estimate (Eqs. 2-3 and 11: p_j(y,E) = q_j(y,E) there).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  * Images are float32 [nz][ny][nx][2]: the two basis components interleaved
+ *    (c_1, c_2) per voxel.  Ray arrays are [n_views][n_rows][n_channels], with a
+ *    trailing pair for two-component ray data.  Measured data is float32
+ *    [2][n_views][n_rows][n_channels] counts, j = 0 (low kVp), 1 (high kVp).
+ *  * Geometry (third-generation helical CT, curved detector):
+ *      source of view v at angle beta_v = start_angle + 2 pi v / views_per_rotation,
+ *        s_v = (sid cos beta_v, sid sin beta_v, z_start + feed v / views_per_rotation);
+ *      channel k at fan angle gamma_k = (k - (K-1)/2 + channel_offset) channel_pitch;
+ *      row r at height w_r = (r - (R-1)/2 + row_offset) row_pitch (mm at the detector);
+ *      ray (v,r,k) leaves s_v along u = (-sdd cos(beta_v+gamma_k), -sdd sin(beta_v+gamma_k), w_r);
+ *      voxel (ix,iy,iz) is centred at (cx + (ix-(nx-1)/2) dx, cy + ..., cz + ...).
+ *    The volume must lie strictly inside the source circle.
+ *  * h(x,y) is Joseph's method: one sample per voxel-centre plane of the dominant
+ *    transaxial axis (x when |u_x| >= |u_y|), bilinear in the other two axes,
+ *    weight (plane spacing) |u| / |u_dominant|; taps outside the volume are zero.
+ *  * `stream` is a cudaStream_t (NULL = the legacy default stream).  All work is
+ *    enqueued on it; calls that return host values synchronise it.
+ *  * Device pointers are borrowed for the duration of the call.  Where a parameter
+ *    says "host or device", a host pointer is detected with cudaPointerGetAttributes
+ *    and staged through the context's device buffers.
+ *  * Every call returns DEAM_OK or an error code; deam_last_error() gives a
+ *    message for the calling thread.  Arguments are validated on the host before
+ *    any launch.  A CUDA error leaves the context unusable (DEAM_ERR_STATE).
+ */
+#ifndef DEAM_H
+#define DEAM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    DEAM_OK = 0,
+    DEAM_ERR_ARG = 1,     /* invalid argument or geometry */
+    DEAM_ERR_CUDA = 2,    /* a CUDA runtime call or kernel failed */
+    DEAM_ERR_OOM = 3,     /* device allocation failed */
+    DEAM_ERR_STATE = 4,   /* call not valid in the context's state (no data, earlier failure) */
+    DEAM_ERR_TIMEOUT = 5, /* a bounded device wait expired */
+    DEAM_ERR_NUMERIC = 6  /* non-finite objective */
+};
+
+enum { DEAM_GEOM_FAN2D = 0, DEAM_GEOM_HELICAL = 1 };
+
+enum {
+    DEAM_MASK_VOXEL_IMAGE = 0, /* m: float32 metal image M [nz][ny][nx]; mask = (A M >= t) */
+    DEAM_MASK_RAY = 1          /* m: uint8 [V][R][K], nonzero = metal-trace ray */
+};
+
+/* Scanner and volume geometry (lengths in mm, angles in rad). */
+typedef struct deam_geometry {
+    int kind; /* DEAM_GEOM_FAN2D (n_rows = 1, feed = 0) or DEAM_GEOM_HELICAL */
+    int nx, ny, nz;
+    double dx, dy, dz;
+    double cx, cy, cz; /* volume centre */
+    double sid, sdd;   /* source-isocentre and source-detector distances */
+    int n_views, views_per_rotation;
+    double start_angle, feed, z_start; /* feed = table travel per rotation */
+    int n_rows;
+    double row_pitch; /* at the detector */
+    int n_channels;
+    double channel_pitch; /* fan angle between channels */
+    double channel_offset, row_offset; /* detector shifts, in cells */
+} deam_geometry;
+
+/* Source spectra I0_j(y,E) = I0[j][E] * bowtie[channel] (Eq. 8: "contains the
+ * spectrum and the bowtie filter").  Bins where both spectra are zero are skipped. */
+typedef struct deam_spectra {
+    int n_e;                 /* energy bins, 1..256 */
+    const double *energy_keV; /* [n_e] bin centres (informational, may be NULL) */
+    const double *I0;        /* [2][n_e] counts per ray per bin, >= 0 */
+    const double *bowtie;    /* [n_channels] factors > 0, or NULL for 1 */
+} deam_spectra;
+
+/* Basis attenuation mu_i(E) of the two components, 1/mm, >= 0 (Eq. 8). */
+typedef struct deam_basis {
+    int n_e;
+    const double *mu; /* [2][n_e] */
+} deam_basis;
+
+typedef struct deam_options {
+    double metal_threshold; /* t of Sec. 2.1 in mm of metal path; <= 0: half the smallest voxel edge */
+    double Z;               /* c-step normaliser; <= 0: max_E(mu_1+mu_2) * max_y sum_x h(x,y) */
+    int clamp_nonneg;       /* 1: clamp c_i >= 0 after each c-step (the paper is silent; default 0) */
+    int reserved[7];        /* zero */
+} deam_options;
+
+typedef struct deam_ctx deam_ctx;
+
+/* Create a context for one scan: validates the geometry, copies the spectra and
+ * attenuation tables to the current CUDA device, allocates the context's device
+ * buffers (measurements, metal mask, per-ray payload, reduction partials, the
+ * projector's volume layouts) and computes the normaliser Z (Appendix-style
+ * surrogate condition sum_{x,i} h mu_i / Z <= 1 for every ray and active bin).
+ * opts may be NULL for defaults.  Returns DEAM_ERR_ARG, DEAM_ERR_OOM or
+ * DEAM_ERR_CUDA on failure (*out is then NULL). */
+int deam_init(const deam_geometry *geom, const deam_spectra *spectra, const deam_basis *basis,
+              const deam_options *opts, deam_ctx **out);
+
+/* Store the measurements d (host or device, float32 [2][V][R][K], counts) as the
+ * nonnegative substitution d~ = max(d, 0) (Sec. 2.1). */
+int deam_set_data(deam_ctx *ctx, const float *d, void *stream);
+
+/* Set the metal trace (Sec. 2.1: rays with T(y) >= t are "metal").  kind =
+ * DEAM_MASK_VOXEL_IMAGE: m is the metal image M (host or device float32
+ * [nz][ny][nx]), forward-projected on the GPU and thresholded at opts.metal_threshold
+ * (T = t counts as metal).  kind = DEAM_MASK_RAY: m is a uint8 ray mask (host or
+ * device), copied.  Until called, no ray is metal (plain DEAM). */
+int deam_set_metal_mask(deam_ctx *ctx, const void *m, int kind, void *stream);
+
+/* Copy the current metal mask (uint8 [V][R][K]) to device memory `mask`. */
+int deam_get_metal_mask(deam_ctx *ctx, uint8_t *mask, void *stream);
+
+/* Forward model at image c (device float32 [nz][ny][nx][2]): line integrals
+ * l_i(y) = sum_x h(x,y) c_i(x) into l (device float32 [V][R][K][2], may be NULL)
+ * and, if g is not NULL, the expected counts g_j(y:c) of Eq. (8) into g (device
+ * float32 [2][V][R][K]). */
+int deam_forward(deam_ctx *ctx, const float *c, float *l, float *g, void *stream);
+
+/* Adjoint of the projector: img_i(x) = sum_y h(x,y) y_i(y), exactly the transpose
+ * of deam_forward's h.  y: device float32 [V][R][K][2]; img: device float32
+ * [nz][ny][nx][2], overwritten.  Gather form: deterministic, no atomics. */
+int deam_backproject(deam_ctx *ctx, const float *y, float *img, void *stream);
+
+/* Per-ray quantities of one MAR-DEAM iteration at image c (device): payload
+ * (device float32 [V][R][K][4]) = (B~_1, B~_2, D_1, D_2) with
+ * B~_i = sum_j S_ij, D_i = sum_j (r_j - 1) S_ij, S_ij = sum_E mu_i(E) q_j(y,E),
+ * r_j = d~_j/g_j off the metal trace and 1 on it (Eqs. 9-11); *F (host, may be
+ * NULL) receives the objective of deam_objective.  Needs deam_set_data. */
+int deam_ray_terms(deam_ctx *ctx, const float *c, float *payload, double *F, void *stream);
+
+/* Run n_iter MAR-DEAM iterations in place on c (host or device float32
+ * [nz][ny][nx][2]).  Each iteration: forward projection with the fused spectral
+ * sums, metal-trace substitution and p-step ratio; the objective
+ * F(c^k) = sum_j sum_{T(y)<t} I(d~_j || g_j(c^k)) (Eq. 5 with Eqs. 2-3) into
+ * hist[k] (host, may be NULL); then the gather backprojection of the payload fused
+ * with the c-step c_i <- c_i - (1/Z) ln(b^_i / b~_i), where b~_i = sum_{y,E} h mu_i q
+ * and b^_i = sum_{y,E} h mu_i p (computed as log1p(delta_i / b~_i) with
+ * delta_i = b^_i - b~_i backprojected directly).  Voxels with b~_i <= 0 or
+ * b^_i <= 0 are left unchanged.  Needs deam_set_data.  Deterministic. */
+int deam_iterate(deam_ctx *ctx, float *c, int n_iter, double *hist, void *stream);
+
+/* F(c) (Eq. 5 over rays off the metal trace) into *out (host). Needs deam_set_data. */
+int deam_objective(deam_ctx *ctx, const float *c, double *out, void *stream);
+
+/* Normaliser Z in use, and the number of (voxel, component) pairs left unchanged
+ * by the last c-step (b~ <= 0 or b^ <= 0). Either pointer may be NULL. */
+int deam_info(deam_ctx *ctx, double *Z, long long *skipped_last);
+
+/* Number of Joseph samples (ray, plane) pairs with at least one tap in the
+ * volume, summed over all rays: the work of one projection (host *n). */
+int deam_count_samples(deam_ctx *ctx, long long *n, void *stream);
+
+/* Per-kernel timing of deam_iterate.  enable = 1 records CUDA events on the
+ * call's stream around every kernel of every iteration (layout build, forward +
+ * epilogue, objective reduction, backprojection + update) and accumulates their
+ * durations; enable = 0 stops.  deam_kernel_times copies the accumulated
+ * milliseconds and launch counts of those four stages into ms[4] and
+ * launches[4] (either may be NULL) and, if reset is nonzero, clears them. */
+int deam_profile(deam_ctx *ctx, int enable);
+int deam_kernel_times(deam_ctx *ctx, double *ms, long long *launches, int reset);
+
+/* Release the context and its device buffers (waits for its work). NULL is a no-op. */
+int deam_destroy(deam_ctx *ctx);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char *deam_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DEAM_H */

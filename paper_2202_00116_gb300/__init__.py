@@ -1,0 +1,273 @@
+"""GB300 (sm_103a) MAR-DEAM: Python binding of libdeam.so.
+
+Argument marshalling only: every step of the reconstruction runs in the CUDA
+kernels behind the C ABI declared in ``include/deam.h``.  PyTorch provides device
+memory and streams.  The binding refuses to run without the compiled library
+(there is no CPU fallback); build it with ``paper_2202_00116_gb300.build.build()``.
+
+Method: MAR-DEAM of Ge et al., "A Metal Artifact Reduction Scheme For Accurate
+Iterative Dual-Energy CT Algorithms" (arXiv 2202.00116), Sec. 2.3: DEAM
+iterations on the I-divergence of Eq. (5) with the polyenergetic model of Eq. (8)
+and the metal-trace substitution of Eqs. (2)-(3) and (11).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdeam.so")
+
+DEAM_OK, DEAM_ERR_ARG, DEAM_ERR_CUDA, DEAM_ERR_OOM, DEAM_ERR_STATE, DEAM_ERR_TIMEOUT, DEAM_ERR_NUMERIC = range(7)
+FAN2D, HELICAL = 0, 1
+MASK_VOXEL_IMAGE, MASK_RAY = 0, 1
+
+
+class deam_geometry(C.Structure):
+    _fields_ = [("kind", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
+                ("cx", C.c_double), ("cy", C.c_double), ("cz", C.c_double),
+                ("sid", C.c_double), ("sdd", C.c_double),
+                ("n_views", C.c_int), ("views_per_rotation", C.c_int),
+                ("start_angle", C.c_double), ("feed", C.c_double), ("z_start", C.c_double),
+                ("n_rows", C.c_int), ("row_pitch", C.c_double),
+                ("n_channels", C.c_int), ("channel_pitch", C.c_double),
+                ("channel_offset", C.c_double), ("row_offset", C.c_double)]
+
+
+class deam_spectra(C.Structure):
+    _fields_ = [("n_e", C.c_int), ("energy_keV", C.POINTER(C.c_double)), ("I0", C.POINTER(C.c_double)),
+                ("bowtie", C.POINTER(C.c_double))]
+
+
+class deam_basis(C.Structure):
+    _fields_ = [("n_e", C.c_int), ("mu", C.POINTER(C.c_double))]
+
+
+class deam_options(C.Structure):
+    _fields_ = [("metal_threshold", C.c_double), ("Z", C.c_double), ("clamp_nonneg", C.c_int),
+                ("reserved", C.c_int * 7)]
+
+
+class DeamError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"deam error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+EXPORTS = ["deam_init", "deam_set_data", "deam_set_metal_mask", "deam_get_metal_mask", "deam_forward",
+           "deam_backproject", "deam_ray_terms", "deam_iterate", "deam_objective", "deam_info",
+           "deam_count_samples", "deam_profile", "deam_kernel_times", "deam_destroy", "deam_last_error"]
+
+
+def lib():
+    """Load libdeam.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2202_00116_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, i, pd = C.c_void_p, C.c_int, C.POINTER(C.c_double)
+        sig = {
+            "deam_init": [C.POINTER(deam_geometry), C.POINTER(deam_spectra), C.POINTER(deam_basis),
+                          C.POINTER(deam_options), C.POINTER(vp)],
+            "deam_set_data": [vp, vp, vp],
+            "deam_set_metal_mask": [vp, vp, i, vp],
+            "deam_get_metal_mask": [vp, vp, vp],
+            "deam_forward": [vp, vp, vp, vp, vp],
+            "deam_backproject": [vp, vp, vp, vp],
+            "deam_ray_terms": [vp, vp, vp, pd, vp],
+            "deam_iterate": [vp, vp, i, pd, vp],
+            "deam_objective": [vp, vp, pd, vp],
+            "deam_info": [vp, pd, C.POINTER(C.c_longlong)],
+            "deam_count_samples": [vp, C.POINTER(C.c_longlong), vp],
+            "deam_profile": [vp, i],
+            "deam_kernel_times": [vp, pd, C.POINTER(C.c_longlong), i],
+            "deam_destroy": [vp],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.deam_last_error.argtypes = []
+        L.deam_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != DEAM_OK:
+        raise DeamError(rc, lib().deam_last_error().decode(errors="replace"))
+
+
+class Deam:
+    """One scan: geometry + spectra + basis tables on a CUDA device.
+
+    Tensors are torch tensors: images float32 [nz, ny, nx, 2]; ray pairs float32
+    [V, R, K, 2]; data float32 [2, V, R, K]; masks uint8 [V, R, K].
+    """
+
+    def __init__(self, geo, I0, mu, bowtie=None, energies=None, metal_threshold=0.0, Z=0.0,
+                 clamp_nonneg=False, device=None):
+        import torch
+        self.torch = torch
+        if device is None:
+            device = torch.cuda.current_device() if torch.cuda.is_available() else 0
+        self.device = torch.device("cuda", device)
+        self.geo = geo
+        self._g = deam_geometry(int(geo.kind), geo.nx, geo.ny, geo.nz, geo.dx, geo.dy, geo.dz, geo.cx, geo.cy,
+                                geo.cz, geo.sid, geo.sdd, geo.n_views, geo.views_per_rotation, geo.start_angle,
+                                geo.feed, geo.z_start, geo.n_rows, geo.row_pitch, geo.n_channels,
+                                geo.channel_pitch, geo.channel_offset, geo.row_offset)
+        self._I0 = np.ascontiguousarray(np.asarray(I0, dtype=np.float64))
+        self._mu = np.ascontiguousarray(np.asarray(mu, dtype=np.float64))
+        nE = self._I0.shape[1]
+        P = C.POINTER(C.c_double)
+        self._bow = None if bowtie is None else np.ascontiguousarray(np.asarray(bowtie, dtype=np.float64))
+        self._E = None if energies is None else np.ascontiguousarray(np.asarray(energies, dtype=np.float64))
+        sp = deam_spectra(nE, self._E.ctypes.data_as(P) if self._E is not None else P(),
+                          self._I0.ctypes.data_as(P), self._bow.ctypes.data_as(P) if self._bow is not None else P())
+        ba = deam_basis(self._mu.shape[1], self._mu.ctypes.data_as(P))
+        op = deam_options(float(metal_threshold), float(Z), int(bool(clamp_nonneg)))
+        h = C.c_void_p()
+        self._h = None
+        if torch.cuda.is_available():
+            with torch.cuda.device(self.device):
+                _check(lib().deam_init(C.byref(self._g), C.byref(sp), C.byref(ba), C.byref(op), C.byref(h)))
+        else:  # host-side validation still runs; without a device the call then fails
+            _check(lib().deam_init(C.byref(self._g), C.byref(sp), C.byref(ba), C.byref(op), C.byref(h)))
+        self._h = h
+
+    # -- helpers --
+    @property
+    def ray_shape(self):
+        return (self.geo.n_views, self.geo.n_rows, self.geo.n_channels)
+
+    @property
+    def img_shape(self):
+        return (self.geo.nz, self.geo.ny, self.geo.nx, 2)
+
+    def _stream(self):
+        return C.c_void_p(self.torch.cuda.current_stream(self.device).cuda_stream)
+
+    def _arg(self, t, shape, dtype, host_ok=False):
+        torch = self.torch
+        if not isinstance(t, torch.Tensor):
+            raise TypeError("expected a torch tensor")
+        if tuple(t.shape) != tuple(shape) or t.dtype != dtype or not t.is_contiguous():
+            raise ValueError(f"expected contiguous {dtype} tensor of shape {tuple(shape)}, got "
+                             f"{t.dtype} {tuple(t.shape)}")
+        if t.is_cuda:
+            if t.device != self.device:
+                raise ValueError(f"tensor on {t.device}, context on {self.device}")
+        elif not host_ok:
+            raise ValueError("expected a CUDA tensor")
+        return C.c_void_p(t.data_ptr())
+
+    # -- API --
+    def set_data(self, d):
+        """Measured counts d [2, V, R, K] (CUDA or host tensor); stored as max(d, 0)."""
+        _check(lib().deam_set_data(self._h, self._arg(d, (2,) + self.ray_shape, self.torch.float32, True),
+                                   self._stream()))
+        if not d.is_cuda:
+            self.torch.cuda.current_stream(self.device).synchronize()
+
+    def set_metal_mask(self, m, kind="ray"):
+        """kind='ray': uint8 [V, R, K]; kind='voxel': float32 metal image [nz, ny, nx]."""
+        torch = self.torch
+        if kind == "ray":
+            p = self._arg(m, self.ray_shape, torch.uint8, True)
+            k = MASK_RAY
+        else:
+            p = self._arg(m, self.img_shape[:3], torch.float32, True)
+            k = MASK_VOXEL_IMAGE
+        _check(lib().deam_set_metal_mask(self._h, p, k, self._stream()))
+        if not m.is_cuda:
+            torch.cuda.current_stream(self.device).synchronize()
+
+    def metal_mask(self):
+        out = self.torch.empty(self.ray_shape, dtype=self.torch.uint8, device=self.device)
+        _check(lib().deam_get_metal_mask(self._h, C.c_void_p(out.data_ptr()), self._stream()))
+        return out
+
+    def forward(self, c, want_l=True, want_g=False):
+        """Line integrals l [V, R, K, 2] and/or expected counts g [2, V, R, K]."""
+        torch = self.torch
+        l = torch.empty(self.ray_shape + (2,), dtype=torch.float32, device=self.device) if want_l else None
+        g = torch.empty((2,) + self.ray_shape, dtype=torch.float32, device=self.device) if want_g else None
+        _check(lib().deam_forward(self._h, self._arg(c, self.img_shape, torch.float32),
+                                  C.c_void_p(l.data_ptr()) if l is not None else None,
+                                  C.c_void_p(g.data_ptr()) if g is not None else None, self._stream()))
+        return l, g
+
+    def backproject(self, y, out=None):
+        torch = self.torch
+        if out is None:
+            out = torch.empty(self.img_shape, dtype=torch.float32, device=self.device)
+        _check(lib().deam_backproject(self._h, self._arg(y, self.ray_shape + (2,), torch.float32),
+                                      self._arg(out, self.img_shape, torch.float32), self._stream()))
+        return out
+
+    def ray_terms(self, c):
+        """(payload [V, R, K, 4] = (B~1, B~2, D1, D2), F)."""
+        torch = self.torch
+        pay = torch.empty(self.ray_shape + (4,), dtype=torch.float32, device=self.device)
+        F = C.c_double()
+        _check(lib().deam_ray_terms(self._h, self._arg(c, self.img_shape, torch.float32),
+                                    C.c_void_p(pay.data_ptr()), C.byref(F), self._stream()))
+        return pay, F.value
+
+    def iterate(self, c, n_iter):
+        """n_iter MAR-DEAM iterations in place on c (CUDA or host tensor); returns
+        the objective history F(c^k), k = 0..n_iter-1, as a numpy array."""
+        hist = np.zeros(max(n_iter, 1), dtype=np.float64)
+        _check(lib().deam_iterate(self._h, self._arg(c, self.img_shape, self.torch.float32, True), int(n_iter),
+                                  hist.ctypes.data_as(C.POINTER(C.c_double)), self._stream()))
+        return hist[:n_iter]
+
+    def objective(self, c):
+        F = C.c_double()
+        _check(lib().deam_objective(self._h, self._arg(c, self.img_shape, self.torch.float32), C.byref(F),
+                                    self._stream()))
+        return F.value
+
+    def info(self):
+        Z = C.c_double()
+        sk = C.c_longlong()
+        _check(lib().deam_info(self._h, C.byref(Z), C.byref(sk)))
+        return Z.value, sk.value
+
+    def count_samples(self):
+        """Joseph samples of one projection (the work unit of ray-samples/s)."""
+        n = C.c_longlong()
+        _check(lib().deam_count_samples(self._h, C.byref(n), self._stream()))
+        return n.value
+
+    def profile(self, enable=True):
+        _check(lib().deam_profile(self._h, int(bool(enable))))
+
+    def kernel_times(self, reset=False):
+        """Accumulated (ms[4], launches[4]) of deam_iterate's stages: layout,
+        forward + epilogue, objective reduction, backprojection + update."""
+        ms = (C.c_double * 4)()
+        n = (C.c_longlong * 4)()
+        _check(lib().deam_kernel_times(self._h, ms, n, int(bool(reset))))
+        return list(ms), list(n)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().deam_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def from_case(case, **kw) -> Deam:
+    return Deam(case.geo, case.I0, case.mu, bowtie=case.bowtie, energies=case.energies, **kw)

@@ -1,0 +1,617 @@
+// C ABI of the sm_103a MAR-DEAM library: argument validation, geometry tables,
+// device buffers and the launch sequence of each entry point (see include/deam.h).
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "deam.h"
+#include "deam_internal.h"
+
+using deam::Geo;
+using deam::Spec;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+const double kPi = 3.14159265358979323846;
+
+bool finite_pos(double x) { return isfinite(x) && x > 0.0; }
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+struct deam_ctx {
+    deam_geometry geo{};
+    Geo G{};
+    Spec S{};
+    int device = 0;
+    double Z = 0.0, threshold = 0.0, mumax = 0.0;
+    int clamp = 0;
+    bool has_data = false, mask_set = false, failed = false;
+    long long nrays = 0, nvox = 0, skipped_last = 0;
+    int n_fwd_blocks = 0, n_slabs = 0;
+    // device buffers
+    float4* view4 = nullptr;
+    float* view_z = nullptr;
+    float2* chan = nullptr;
+    float2* row = nullptr;
+    float* bowtie = nullptr;
+    float* dt = nullptr;
+    uint8_t* mask = nullptr;
+    float4* payload = nullptr;
+    float4* volX = nullptr;
+    float4* volY = nullptr;
+    double* partial = nullptr;
+    double* scal = nullptr;  // [0]: last reduction result
+    double* hist = nullptr;
+    int hist_cap = 0;
+    int2* slab_views = nullptr;
+    unsigned long long* skipped = nullptr;
+    float2* c_stage = nullptr;
+    // per-kernel timing of deam_iterate (deam_profile)
+    bool prof = false;
+    double prof_ms[4] = {0, 0, 0, 0};
+    long long prof_n[4] = {0, 0, 0, 0};
+};
+
+#define CK(x)                                                                                  \
+    do {                                                                                       \
+        cudaError_t e_ = (x);                                                                  \
+        if (e_ != cudaSuccess) {                                                               \
+            ctx->failed = true;                                                                \
+            return fail(e_ == cudaErrorMemoryAllocation ? DEAM_ERR_OOM : DEAM_ERR_CUDA,        \
+                        std::string(#x) + ": " + cudaGetErrorString(e_));                      \
+        }                                                                                      \
+    } while (0)
+
+#define CHECK_CTX(ctx)                                                              \
+    do {                                                                            \
+        if (!(ctx)) return fail(DEAM_ERR_ARG, "null context");                      \
+        if ((ctx)->failed) return fail(DEAM_ERR_STATE, "context failed earlier"); \
+    } while (0)
+
+template <typename T>
+static cudaError_t dalloc(T** p, size_t n) {
+    return cudaMalloc((void**)p, sizeof(T) * std::max<size_t>(n, 1));
+}
+
+static void free_ctx(deam_ctx* c) {
+    void* ptrs[] = {c->view4, c->view_z, c->chan, c->row, c->bowtie, c->dt, c->mask, c->payload,
+                    c->volX, c->volY, c->partial, c->scal, c->hist, c->slab_views, c->skipped, c->c_stage};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete c;
+}
+
+static std::string validate(const deam_geometry* g, const deam_spectra* s, const deam_basis* b) {
+    if (!g || !s || !b) return "geometry, spectra and basis must not be NULL";
+    if (g->kind != DEAM_GEOM_FAN2D && g->kind != DEAM_GEOM_HELICAL) return "geometry.kind must be FAN2D or HELICAL";
+    if (g->nx < 1 || g->ny < 1 || g->nz < 1) return "volume dimensions must be >= 1";
+    if (!finite_pos(g->dx) || !finite_pos(g->dy) || !finite_pos(g->dz)) return "voxel sizes must be finite and > 0";
+    if (!isfinite(g->cx) || !isfinite(g->cy) || !isfinite(g->cz)) return "volume centre must be finite";
+    if (!finite_pos(g->sid) || !finite_pos(g->sdd) || g->sdd <= g->sid) return "need 0 < sid < sdd";
+    if (g->n_views < 1 || g->views_per_rotation < 1) return "n_views and views_per_rotation must be >= 1";
+    if (g->n_rows < 1 || g->n_channels < 1) return "detector must have >= 1 row and channel";
+    if (!finite_pos(g->channel_pitch)) return "channel_pitch must be finite and > 0";
+    if (g->n_rows > 1 && !finite_pos(g->row_pitch)) return "row_pitch must be finite and > 0";
+    if (!isfinite(g->start_angle) || !isfinite(g->feed) || !isfinite(g->z_start) || !isfinite(g->channel_offset) ||
+        !isfinite(g->row_offset) || !isfinite(g->row_pitch))
+        return "geometry values must be finite";
+    if (g->kind == DEAM_GEOM_FAN2D && (g->n_rows != 1 || g->feed != 0.0))
+        return "FAN2D geometry needs n_rows = 1 and feed = 0";
+    if ((double)g->channel_pitch * g->n_channels >= kPi) return "fan wider than pi";
+    // the volume (plus one voxel of interpolation support) must lie inside the source circle
+    double rmax = 0.0;
+    for (int sx = -1; sx <= 1; sx += 2)
+        for (int sy = -1; sy <= 1; sy += 2) {
+            double x = g->cx + sx * (g->nx + 1) / 2.0 * g->dx, y = g->cy + sy * (g->ny + 1) / 2.0 * g->dy;
+            rmax = std::max(rmax, sqrt(x * x + y * y));
+        }
+    if (rmax >= 0.98 * g->sid) return "volume must lie inside the source circle";
+    // 32-bit index limits of the kernels
+    const double big = 2147483647.0;
+    if ((double)g->nx * (g->nz + 2) * (g->ny + 1) >= big || (double)g->ny * (g->nz + 2) * (g->nx + 1) >= big)
+        return "volume too large for 32-bit plane indexing";
+    if ((double)g->n_views * g->n_rows >= big) return "too many views x rows";
+    if (s->n_e < 1 || s->n_e > deam::kMaxE) return "spectra.n_e must be in [1, 256]";
+    if (b->n_e != s->n_e) return "basis.n_e must equal spectra.n_e";
+    if (!s->I0 || !b->mu) return "spectra.I0 and basis.mu must not be NULL";
+    bool any = false;
+    for (int i = 0; i < 2 * s->n_e; ++i) {
+        if (!isfinite(s->I0[i]) || s->I0[i] < 0.0) return "I0 must be finite and >= 0";
+        if (!isfinite(b->mu[i]) || b->mu[i] < 0.0) return "mu must be finite and >= 0";
+        any = any || s->I0[i] > 0.0;
+    }
+    if (!any) return "both spectra are empty";
+    if (s->bowtie)
+        for (int k = 0; k < g->n_channels; ++k)
+            if (!finite_pos(s->bowtie[k])) return "bowtie factors must be finite and > 0";
+    return "";
+}
+
+// View range [lo, hi] whose rays can put a sample into the z-range of slab s
+// (voxel centres +- one slice of interpolation support).
+static int2 slab_view_range(const deam_geometry& g, int s) {
+    const int z0 = s * deam::kSlab, z1 = std::min(g.nz, z0 + deam::kSlab) - 1;
+    if (g.feed == 0.0 || g.nz == 1) return make_int2(0, g.n_views - 1);
+    const double Z0 = g.cz - (g.nz - 1) / 2.0 * g.dz;
+    const double zlo = Z0 + (z0 - 1) * g.dz, zhi = Z0 + (z1 + 1) * g.dz;
+    double rmax = 0.0;
+    for (int sx = -1; sx <= 1; sx += 2)
+        for (int sy = -1; sy <= 1; sy += 2) {
+            double x = g.cx + sx * (g.nx + 1) / 2.0 * g.dx, y = g.cy + sy * (g.ny + 1) / 2.0 * g.dy;
+            rmax = std::max(rmax, sqrt(x * x + y * y));
+        }
+    const double t0 = (g.sid - rmax) / g.sdd, t1 = (g.sid + rmax) / g.sdd;
+    const double w0 = (0 - (g.n_rows - 1) / 2.0 + g.row_offset) * g.row_pitch;
+    const double w1 = (g.n_rows - 1 - (g.n_rows - 1) / 2.0 + g.row_offset) * g.row_pitch;
+    const double tw[4] = {t0 * w0, t0 * w1, t1 * w0, t1 * w1};
+    const double twmax = *std::max_element(tw, tw + 4), twmin = *std::min_element(tw, tw + 4);
+    // z* = s_z + t w  in [zlo, zhi]  <=>  s_z in [zlo - max(t w), zhi - min(t w)]
+    const double szlo = zlo - twmax, szhi = zhi - twmin;
+    double va = (szlo - g.z_start) * g.views_per_rotation / g.feed;
+    double vb = (szhi - g.z_start) * g.views_per_rotation / g.feed;
+    if (va > vb) std::swap(va, vb);
+    long long lo = (long long)floor(va) - 2, hi = (long long)ceil(vb) + 2;
+    lo = std::max(lo, 0LL);
+    hi = std::min(hi, (long long)g.n_views - 1);
+    if (lo > hi) return make_int2(1, 0);
+    return make_int2((int)lo, (int)hi);
+}
+
+static int build_layouts(deam_ctx* ctx, const float2* c, const float* m, int ones, cudaStream_t s) {
+    CK(deam::launch_layout(c, m, ones, ctx->volX, ctx->volY, ctx->geo.nx, ctx->geo.ny, ctx->geo.nz, s));
+    return DEAM_OK;
+}
+
+static deam::FwdArgs fwd_args(deam_ctx* ctx) {
+    deam::FwdArgs A{};
+    A.volX = ctx->volX;
+    A.volY = ctx->volY;
+    A.bowtie = ctx->bowtie;
+    A.partial = ctx->partial;
+    return A;
+}
+
+extern "C" {
+
+const char* deam_last_error(void) { return g_err.c_str(); }
+
+int deam_init(const deam_geometry* geom, const deam_spectra* spectra, const deam_basis* basis,
+              const deam_options* opts, deam_ctx** out) {
+    if (!out) return fail(DEAM_ERR_ARG, "out must not be NULL");
+    *out = nullptr;
+    std::string why = validate(geom, spectra, basis);
+    if (!why.empty()) return fail(DEAM_ERR_ARG, why);
+    deam_options o{};
+    if (opts) o = *opts;
+    if (!isfinite(o.metal_threshold) || !isfinite(o.Z)) return fail(DEAM_ERR_ARG, "options must be finite");
+
+    deam_ctx* ctx = new deam_ctx();
+    const deam_geometry& g = *geom;
+    ctx->geo = g;
+    if (cudaGetDevice(&ctx->device) != cudaSuccess) {
+        delete ctx;
+        return fail(DEAM_ERR_CUDA, "no CUDA device");
+    }
+    ctx->nrays = (long long)g.n_views * g.n_rows * g.n_channels;
+    ctx->nvox = (long long)g.nx * g.ny * g.nz;
+    ctx->clamp = o.clamp_nonneg ? 1 : 0;
+    ctx->threshold = o.metal_threshold > 0.0 ? o.metal_threshold
+                                             : 0.5 * std::min(g.dx, std::min(g.dy, g.nz > 1 ? g.dz : g.dx));
+    ctx->n_slabs = (g.nz + deam::kSlab - 1) / deam::kSlab;
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    ctx->n_fwd_blocks = (int)std::min<long long>((ctx->nrays + deam::kFwdThreads - 1) / deam::kFwdThreads,
+                                                 (long long)sms * 16);
+
+    // ---- geometry tables (double on the host, rounded once to float) ----
+    const double X0 = g.cx - (g.nx - 1) / 2.0 * g.dx, Y0 = g.cy - (g.ny - 1) / 2.0 * g.dy,
+                 Z0 = g.cz - (g.nz - 1) / 2.0 * g.dz;
+    std::vector<float4> v4(g.n_views);
+    std::vector<float> vz(g.n_views);
+    for (int v = 0; v < g.n_views; ++v) {
+        const double beta = g.start_angle + 2.0 * kPi * v / g.views_per_rotation;
+        const double sx = g.sid * cos(beta), sy = g.sid * sin(beta);
+        const double sz = g.z_start + g.feed * v / g.views_per_rotation;
+        v4[v] = make_float4((float)((sx - X0) / g.dx), (float)((sy - Y0) / g.dy), (float)cos(beta), (float)sin(beta));
+        vz[v] = (float)((sz - Z0) / g.dz);
+    }
+    std::vector<float2> ch(g.n_channels), rw(g.n_rows);
+    for (int k = 0; k < g.n_channels; ++k) {
+        const double gam = (k - (g.n_channels - 1) / 2.0 + g.channel_offset) * g.channel_pitch;
+        ch[k] = make_float2((float)cos(gam), (float)sin(gam));
+    }
+    for (int r = 0; r < g.n_rows; ++r) {
+        const double w = (r - (g.n_rows - 1) / 2.0 + g.row_offset) * g.row_pitch;
+        rw[r] = make_float2((float)(w / g.dz), (float)sqrt(1.0 + (w / g.sdd) * (w / g.sdd)));
+    }
+    std::vector<int2> sv(ctx->n_slabs);
+    for (int s = 0; s < ctx->n_slabs; ++s) sv[s] = slab_view_range(g, s);
+
+    Geo& G = ctx->G;
+    G.nx = g.nx; G.ny = g.ny; G.nz = g.nz; G.V = g.n_views; G.R = g.n_rows; G.K = g.n_channels;
+    G.dx = (float)g.dx; G.dy = (float)g.dy;
+    G.dx_sdd = (float)(g.dx / g.sdd); G.dy_sdd = (float)(g.dy / g.sdd);
+    G.dx_dy = (float)(g.dx / g.dy); G.dy_dx = (float)(g.dy / g.dx);
+    G.omega0 = (float)((0 - (g.n_rows - 1) / 2.0 + g.row_offset) * g.row_pitch / g.dz);
+    G.domega = (float)(g.row_pitch / g.dz);
+    G.chan_c0 = (float)((g.n_channels - 1) / 2.0 - g.channel_offset);
+    G.inv_dgamma = (float)(1.0 / g.channel_pitch);
+    G.vox_reach_mm = (float)(std::max(g.dx, g.dy) * 1.001);
+
+    // ---- spectral tables ----
+    Spec& S = ctx->S;
+    const int nE = spectra->n_e;
+    S.e_lo = nE;
+    S.e_hi = 0;
+    const double log2e = 1.4426950408889634;
+    double mumax = 0.0;
+    for (int e = 0; e < nE; ++e) {
+        const double il = spectra->I0[e], ih = spectra->I0[nE + e];
+        const double m1 = basis->mu[e], m2 = basis->mu[nE + e];
+        S.mu1l2[e] = (float)(m1 * log2e);
+        S.mu2l2[e] = (float)(m2 * log2e);
+        S.mu1[e] = (float)m1;
+        S.mu2[e] = (float)m2;
+        S.i0l[e] = (float)il;
+        S.i0h[e] = (float)ih;
+        if (il > 0.0 || ih > 0.0) {
+            S.e_lo = std::min(S.e_lo, e);
+            S.e_hi = std::max(S.e_hi, e + 1);
+            mumax = std::max(mumax, m1 + m2);
+        }
+    }
+    ctx->mumax = mumax;
+
+    // ---- device buffers ----
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const size_t volx = (size_t)nx * (nz + 2) * (ny + 1), voly = (size_t)ny * (nz + 2) * (nx + 1);
+    cudaError_t e = cudaSuccess;
+    auto A = [&](cudaError_t r) {
+        if (e == cudaSuccess) e = r;
+    };
+    A(dalloc(&ctx->view4, g.n_views));
+    A(dalloc(&ctx->view_z, g.n_views));
+    A(dalloc(&ctx->chan, g.n_channels));
+    A(dalloc(&ctx->row, g.n_rows));
+    A(dalloc(&ctx->slab_views, ctx->n_slabs));
+    A(dalloc(&ctx->dt, (size_t)2 * ctx->nrays));
+    A(dalloc(&ctx->mask, (size_t)ctx->nrays));
+    A(dalloc(&ctx->payload, (size_t)ctx->nrays));
+    A(dalloc(&ctx->volX, volx));
+    A(dalloc(&ctx->volY, voly));
+    A(dalloc(&ctx->partial, (size_t)ctx->n_fwd_blocks));
+    A(dalloc(&ctx->scal, 4));
+    A(dalloc(&ctx->skipped, 1));
+    if (spectra->bowtie) A(dalloc(&ctx->bowtie, g.n_channels));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_ctx(ctx);
+        return fail(e == cudaErrorMemoryAllocation ? DEAM_ERR_OOM : DEAM_ERR_CUDA,
+                    std::string("device allocation failed: ") + cudaGetErrorString(e));
+    }
+    G.view4 = ctx->view4;
+    G.view_z = ctx->view_z;
+    G.chan = ctx->chan;
+    G.row = ctx->row;
+    A(cudaMemcpy(ctx->view4, v4.data(), sizeof(float4) * v4.size(), cudaMemcpyHostToDevice));
+    A(cudaMemcpy(ctx->view_z, vz.data(), sizeof(float) * vz.size(), cudaMemcpyHostToDevice));
+    A(cudaMemcpy(ctx->chan, ch.data(), sizeof(float2) * ch.size(), cudaMemcpyHostToDevice));
+    A(cudaMemcpy(ctx->row, rw.data(), sizeof(float2) * rw.size(), cudaMemcpyHostToDevice));
+    A(cudaMemcpy(ctx->slab_views, sv.data(), sizeof(int2) * sv.size(), cudaMemcpyHostToDevice));
+    if (spectra->bowtie) {
+        std::vector<float> bt(g.n_channels);
+        for (int k = 0; k < g.n_channels; ++k) bt[k] = (float)spectra->bowtie[k];
+        A(cudaMemcpy(ctx->bowtie, bt.data(), sizeof(float) * bt.size(), cudaMemcpyHostToDevice));
+    }
+    A(cudaMemset(ctx->mask, 0, (size_t)ctx->nrays));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_ctx(ctx);
+        return fail(DEAM_ERR_CUDA, std::string("table upload failed: ") + cudaGetErrorString(e));
+    }
+
+    // ---- normaliser Z = max_E(mu1+mu2) * max_y sum_x h(x,y) (projection of ones) ----
+    if (o.Z > 0.0) {
+        ctx->Z = o.Z;
+    } else {
+        cudaStream_t s = 0;
+        int rc = build_layouts(ctx, nullptr, nullptr, 1, s);
+        if (rc != DEAM_OK) {
+            std::string m = g_err;
+            free_ctx(ctx);
+            return fail(rc, m);
+        }
+        deam::FwdArgs FA = fwd_args(ctx);
+        e = deam::launch_forward(deam::FWD_MAX, ctx->G, ctx->S, FA, ctx->n_fwd_blocks, s);
+        if (e == cudaSuccess) e = deam::launch_sum_partials(ctx->partial, ctx->n_fwd_blocks, ctx->scal, 1, s);
+        double hmax = 0.0;
+        if (e == cudaSuccess) e = cudaMemcpy(&hmax, ctx->scal, sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            free_ctx(ctx);
+            return fail(DEAM_ERR_CUDA, std::string("normaliser projection failed: ") + cudaGetErrorString(e));
+        }
+        ctx->Z = mumax * hmax;
+        if (!(ctx->Z > 0.0)) {
+            free_ctx(ctx);
+            return fail(DEAM_ERR_ARG, "normaliser Z is zero: no ray meets the volume or mu = 0");
+        }
+    }
+    *out = ctx;
+    return DEAM_OK;
+}
+
+int deam_destroy(deam_ctx* ctx) {
+    if (!ctx) return DEAM_OK;
+    DeviceGuard dg(ctx->device);
+    cudaDeviceSynchronize();
+    free_ctx(ctx);
+    return DEAM_OK;
+}
+
+int deam_info(deam_ctx* ctx, double* Z, long long* skipped_last) {
+    if (!ctx) return fail(DEAM_ERR_ARG, "null context");
+    if (Z) *Z = ctx->Z;
+    if (skipped_last) *skipped_last = ctx->skipped_last;
+    return DEAM_OK;
+}
+
+int deam_set_data(deam_ctx* ctx, const float* d, void* stream) {
+    CHECK_CTX(ctx);
+    if (!d) return fail(DEAM_ERR_ARG, "d must not be NULL");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long n = 2 * ctx->nrays;
+    if (is_device_ptr(d)) {
+        CK(deam::launch_clamp_copy(d, ctx->dt, n, s));
+    } else {
+        CK(cudaMemcpyAsync(ctx->dt, d, sizeof(float) * n, cudaMemcpyHostToDevice, s));
+        CK(deam::launch_clamp_copy(ctx->dt, ctx->dt, n, s));
+    }
+    ctx->has_data = true;
+    return DEAM_OK;
+}
+
+int deam_set_metal_mask(deam_ctx* ctx, const void* m, int kind, void* stream) {
+    CHECK_CTX(ctx);
+    if (!m) return fail(DEAM_ERR_ARG, "m must not be NULL");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool dev = is_device_ptr(m);
+    if (kind == DEAM_MASK_RAY) {
+        CK(cudaMemcpyAsync(ctx->mask, m, (size_t)ctx->nrays, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                           s));
+    } else if (kind == DEAM_MASK_VOXEL_IMAGE) {
+        const float* M = (const float*)m;
+        if (!dev) {
+            // the payload buffer (16 B per ray) is free between calls: stage M there
+            if ((long long)sizeof(float4) * ctx->nrays < (long long)sizeof(float) * ctx->nvox)
+                return fail(DEAM_ERR_ARG, "host metal image larger than the staging buffer; pass device memory");
+            CK(cudaMemcpyAsync(ctx->payload, M, sizeof(float) * ctx->nvox, cudaMemcpyHostToDevice, s));
+            M = (const float*)ctx->payload;
+        }
+        int rc = build_layouts(ctx, nullptr, M, 0, s);
+        if (rc != DEAM_OK) return rc;
+        deam::FwdArgs A = fwd_args(ctx);
+        A.mask_out = ctx->mask;
+        A.threshold = (float)ctx->threshold;
+        CK(deam::launch_forward(deam::FWD_MASK, ctx->G, ctx->S, A, ctx->n_fwd_blocks, s));
+    } else {
+        return fail(DEAM_ERR_ARG, "unknown mask kind");
+    }
+    ctx->mask_set = true;
+    return DEAM_OK;
+}
+
+int deam_get_metal_mask(deam_ctx* ctx, uint8_t* mask, void* stream) {
+    CHECK_CTX(ctx);
+    if (!mask) return fail(DEAM_ERR_ARG, "mask must not be NULL");
+    DeviceGuard dg(ctx->device);
+    CK(cudaMemcpyAsync(mask, ctx->mask, (size_t)ctx->nrays, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return DEAM_OK;
+}
+
+int deam_forward(deam_ctx* ctx, const float* c, float* l, float* g, void* stream) {
+    CHECK_CTX(ctx);
+    if (!c || (!l && !g)) return fail(DEAM_ERR_ARG, "need c and at least one of l, g");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = build_layouts(ctx, (const float2*)c, nullptr, 0, s);
+    if (rc != DEAM_OK) return rc;
+    deam::FwdArgs A = fwd_args(ctx);
+    A.l_out = (float2*)l;
+    A.g_out = g;
+    CK(deam::launch_forward(g ? deam::FWD_LINE_G : deam::FWD_LINE, ctx->G, ctx->S, A, ctx->n_fwd_blocks, s));
+    return DEAM_OK;
+}
+
+int deam_backproject(deam_ctx* ctx, const float* y, float* img, void* stream) {
+    CHECK_CTX(ctx);
+    if (!y || !img) return fail(DEAM_ERR_ARG, "y and img must not be NULL");
+    DeviceGuard dg(ctx->device);
+    deam::BwdArgs B{};
+    B.rays2 = (const float2*)y;
+    B.img = (float2*)img;
+    B.slab_views = ctx->slab_views;
+    CK(deam::launch_backward(0, ctx->G, B, (cudaStream_t)stream));
+    return DEAM_OK;
+}
+
+static int ray_terms(deam_ctx* ctx, const float2* c, float4* payload, double* F, double* F_dev, cudaStream_t s) {
+    int rc = build_layouts(ctx, c, nullptr, 0, s);
+    if (rc != DEAM_OK) return rc;
+    deam::FwdArgs A = fwd_args(ctx);
+    A.dt = ctx->dt;
+    A.mask = ctx->mask_set ? ctx->mask : nullptr;
+    A.payload = payload;
+    CK(deam::launch_forward(deam::FWD_DEAM, ctx->G, ctx->S, A, ctx->n_fwd_blocks, s));
+    CK(deam::launch_sum_partials(ctx->partial, ctx->n_fwd_blocks, F_dev, 0, s));
+    if (F) {
+        CK(cudaMemcpyAsync(F, F_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return DEAM_OK;
+}
+
+int deam_ray_terms(deam_ctx* ctx, const float* c, float* payload, double* F, void* stream) {
+    CHECK_CTX(ctx);
+    if (!c || !payload) return fail(DEAM_ERR_ARG, "c and payload must not be NULL");
+    if (!ctx->has_data) return fail(DEAM_ERR_STATE, "deam_set_data has not been called");
+    DeviceGuard dg(ctx->device);
+    return ray_terms(ctx, (const float2*)c, (float4*)payload, F, ctx->scal, (cudaStream_t)stream);
+}
+
+int deam_objective(deam_ctx* ctx, const float* c, double* out, void* stream) {
+    CHECK_CTX(ctx);
+    if (!c || !out) return fail(DEAM_ERR_ARG, "c and out must not be NULL");
+    if (!ctx->has_data) return fail(DEAM_ERR_STATE, "deam_set_data has not been called");
+    DeviceGuard dg(ctx->device);
+    int rc = ray_terms(ctx, (const float2*)c, ctx->payload, out, ctx->scal, (cudaStream_t)stream);
+    if (rc == DEAM_OK && !isfinite(*out)) return fail(DEAM_ERR_NUMERIC, "objective is not finite");
+    return rc;
+}
+
+int deam_iterate(deam_ctx* ctx, float* c, int n_iter, double* hist, void* stream) {
+    CHECK_CTX(ctx);
+    if (!c) return fail(DEAM_ERR_ARG, "c must not be NULL");
+    if (n_iter < 0) return fail(DEAM_ERR_ARG, "n_iter must be >= 0");
+    if (!ctx->has_data) return fail(DEAM_ERR_STATE, "deam_set_data has not been called");
+    if (n_iter == 0) return DEAM_OK;
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    float2* cd = (float2*)c;
+    const bool host = !is_device_ptr(c);
+    if (host) {
+        if (!ctx->c_stage) CK(dalloc(&ctx->c_stage, (size_t)ctx->nvox));
+        CK(cudaMemcpyAsync(ctx->c_stage, c, sizeof(float2) * ctx->nvox, cudaMemcpyHostToDevice, s));
+        cd = ctx->c_stage;
+    }
+    if (ctx->hist_cap < n_iter) {
+        if (ctx->hist) CK(cudaFree(ctx->hist));
+        ctx->hist = nullptr;
+        ctx->hist_cap = 0;
+        CK(dalloc(&ctx->hist, (size_t)n_iter));
+        ctx->hist_cap = n_iter;
+    }
+    deam::BwdArgs B{};
+    B.payload = ctx->payload;
+    B.img = cd;
+    B.slab_views = ctx->slab_views;
+    B.invZ = (float)(1.0 / ctx->Z);
+    B.clamp_nonneg = ctx->clamp;
+    B.skipped = ctx->skipped;
+    std::vector<cudaEvent_t> ev;
+    if (ctx->prof) {
+        ev.resize((size_t)5 * n_iter);
+        for (auto& x : ev) CK(cudaEventCreate(&x));
+    }
+    deam::FwdArgs A = fwd_args(ctx);
+    A.dt = ctx->dt;
+    A.mask = ctx->mask_set ? ctx->mask : nullptr;
+    A.payload = ctx->payload;
+    for (int it = 0; it < n_iter; ++it) {
+        cudaEvent_t* e = ctx->prof ? &ev[(size_t)5 * it] : nullptr;
+        if (e) CK(cudaEventRecord(e[0], s));
+        int rc = build_layouts(ctx, cd, nullptr, 0, s);
+        if (rc != DEAM_OK) return rc;
+        if (e) CK(cudaEventRecord(e[1], s));
+        CK(deam::launch_forward(deam::FWD_DEAM, ctx->G, ctx->S, A, ctx->n_fwd_blocks, s));
+        if (e) CK(cudaEventRecord(e[2], s));
+        CK(deam::launch_sum_partials(ctx->partial, ctx->n_fwd_blocks, ctx->hist + it, 0, s));
+        CK(cudaMemsetAsync(ctx->skipped, 0, sizeof(unsigned long long), s));
+        if (e) CK(cudaEventRecord(e[3], s));
+        CK(deam::launch_backward(1, ctx->G, B, s));
+        if (e) CK(cudaEventRecord(e[4], s));
+    }
+    unsigned long long sk = 0;
+    CK(cudaMemcpyAsync(&sk, ctx->skipped, sizeof(sk), cudaMemcpyDeviceToHost, s));
+    std::vector<double> h(n_iter);
+    CK(cudaMemcpyAsync(h.data(), ctx->hist, sizeof(double) * n_iter, cudaMemcpyDeviceToHost, s));
+    if (host) CK(cudaMemcpyAsync(c, ctx->c_stage, sizeof(float2) * ctx->nvox, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    ctx->skipped_last = (long long)sk;
+    if (ctx->prof) {
+        const int nl[4] = {2, 1, 1, 1};
+        for (int it = 0; it < n_iter; ++it)
+            for (int j = 0; j < 4; ++j) {
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, ev[(size_t)5 * it + j], ev[(size_t)5 * it + j + 1]));
+                ctx->prof_ms[j] += ms;
+                ctx->prof_n[j] += nl[j];
+            }
+        for (auto& x : ev) cudaEventDestroy(x);
+    }
+    if (hist) memcpy(hist, h.data(), sizeof(double) * n_iter);
+    for (double v : h)
+        if (!isfinite(v)) return fail(DEAM_ERR_NUMERIC, "objective became non-finite");
+    return DEAM_OK;
+}
+
+int deam_count_samples(deam_ctx* ctx, long long* n, void* stream) {
+    CHECK_CTX(ctx);
+    if (!n) return fail(DEAM_ERR_ARG, "n must not be NULL");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    deam::FwdArgs A = fwd_args(ctx);
+    CK(deam::launch_forward(deam::FWD_COUNT, ctx->G, ctx->S, A, ctx->n_fwd_blocks, s));
+    CK(deam::launch_sum_partials(ctx->partial, ctx->n_fwd_blocks, ctx->scal + 1, 0, s));
+    double v = 0.0;
+    CK(cudaMemcpyAsync(&v, ctx->scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *n = (long long)llround(v);
+    return DEAM_OK;
+}
+
+int deam_profile(deam_ctx* ctx, int enable) {
+    CHECK_CTX(ctx);
+    ctx->prof = enable != 0;
+    return DEAM_OK;
+}
+
+int deam_kernel_times(deam_ctx* ctx, double* ms, long long* launches, int reset) {
+    if (!ctx) return fail(DEAM_ERR_ARG, "null context");
+    for (int j = 0; j < 4; ++j) {
+        if (ms) ms[j] = ctx->prof_ms[j];
+        if (launches) launches[j] = ctx->prof_n[j];
+        if (reset) {
+            ctx->prof_ms[j] = 0.0;
+            ctx->prof_n[j] = 0;
+        }
+    }
+    return DEAM_OK;
+}
+
+}  // extern "C"

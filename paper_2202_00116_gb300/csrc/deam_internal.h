@@ -1,0 +1,121 @@
+// Internal declarations shared by the kernels (deam_kernels.cu) and the C ABI
+// (deam_api.cu) of the sm_103a MAR-DEAM library.  Not installed.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace deam {
+
+constexpr int kMaxE = 256;        // energy bins carried in the kernel-parameter tables
+constexpr int kFwdThreads = 128;  // rays per forward block
+constexpr int kTileX = 16;        // backprojector column tile (x)
+constexpr int kTileY = 8;         // backprojector column tile (y)
+constexpr int kSlab = 16;         // backprojector z-slab (voxels per column per block)
+
+// Geometry in voxel-index units, as read by both projector directions.  Every
+// per-ray quantity is derived from these tables by ray_inplane()/row terms with
+// explicitly rounded FP32 operations, so the forward and the gather-backward
+// kernels compute bit-identical sample positions and weights.
+struct Geo {
+    int nx, ny, nz, V, R, K;
+    float dx, dy;            // voxel edge lengths (mm)
+    float dx_sdd, dy_sdd;    // dx / sdd, dy / sdd
+    float dx_dy, dy_dx;      // dx / dy, dy / dx
+    const float4* view4;     // [V] (sigma_x, sigma_y, cos beta, sin beta); sigma = source in index units
+    const float* view_z;     // [V] sigma_z = (s_z - Z0) / dz
+    const float2* chan;      // [K] (cos gamma_k, sin gamma_k)
+    const float2* row;       // [R] (omega_r = w_r / dz, sqrt(1 + (w_r/sdd)^2))
+    // approximate, only for candidate ranges in the gather backprojector
+    float omega0, domega;    // omega_r ~= omega0 + r * domega
+    float chan_c0, inv_dgamma;  // channel coordinate = gamma / dgamma + chan_c0
+    float vox_reach_mm;      // max(dx, dy): reach of a voxel's bilinear footprint in-plane
+};
+
+// Spectral model tables (kernel parameters: they live in the constant bank).
+struct Spec {
+    int e_lo, e_hi;                  // active bins [e_lo, e_hi)
+    float mu1l2[kMaxE], mu2l2[kMaxE];  // mu_i(E) * log2(e), 1/mm
+    float mu1[kMaxE], mu2[kMaxE];      // mu_i(E), 1/mm
+    float i0l[kMaxE], i0h[kMaxE];      // I0_j(E), counts
+};
+
+struct InPlane {
+    int axis;      // 0: x-dominant (planes ix), 1: y-dominant (planes iy)
+    float aq, bq;  // fq(p) = aq + p bq: intercept with plane p on the other transaxial axis (index units)
+    float tau0, kappa;  // ray parameter t(p) = tau0 + p kappa (fraction of u)
+    float Lxy;     // (plane spacing) / |d_dominant|; times the row factor gives Joseph's L
+};
+
+// In-plane ray parameters of (view, channel).  Explicitly rounded operations
+// (no contraction freedom) make the result identical wherever it is inlined.
+__device__ __forceinline__ InPlane ray_inplane(const Geo& G, float4 vw, float2 ch) {
+    // d_k = -(cos(beta + gamma), sin(beta + gamma)) by the angle-sum identities
+    const float dxk = __fmaf_rn(vw.w, ch.y, -__fmul_rn(vw.z, ch.x));
+    const float dyk = -__fmaf_rn(vw.w, ch.x, __fmul_rn(vw.z, ch.y));
+    InPlane r;
+    if (fabsf(dxk) >= fabsf(dyk)) {
+        r.axis = 0;
+        const float m = __fmul_rn(__fdiv_rn(dyk, dxk), G.dx_dy);
+        r.aq = __fmaf_rn(-vw.x, m, vw.y);
+        r.bq = m;
+        r.kappa = __fdiv_rn(G.dx_sdd, dxk);
+        r.tau0 = __fmul_rn(-vw.x, r.kappa);
+        r.Lxy = __fdiv_rn(G.dx, fabsf(dxk));
+    } else {
+        r.axis = 1;
+        const float m = __fmul_rn(__fdiv_rn(dxk, dyk), G.dy_dx);
+        r.aq = __fmaf_rn(-vw.y, m, vw.x);
+        r.bq = m;
+        r.kappa = __fdiv_rn(G.dy_sdd, dyk);
+        r.tau0 = __fmul_rn(-vw.y, r.kappa);
+        r.Lxy = __fdiv_rn(G.dy, fabsf(dyk));
+    }
+    return r;
+}
+
+// z-intercept of the ray of row r at plane p: fz = az + p bz.
+__device__ __forceinline__ float row_fz(const InPlane& ip, float sigma_z, float omega, float p) {
+    const float az = __fmaf_rn(ip.tau0, omega, sigma_z);
+    const float bz = __fmul_rn(ip.kappa, omega);
+    return __fmaf_rn(p, bz, az);
+}
+
+// ---------------------------------------------------------------------------
+// kernel launchers (deam_kernels.cu)
+// ---------------------------------------------------------------------------
+enum FwdMode { FWD_LINE = 0, FWD_LINE_G = 1, FWD_DEAM = 2, FWD_MASK = 3, FWD_MAX = 4, FWD_COUNT = 5 };
+
+struct FwdArgs {
+    const float4* volX;   // [nx][nz+2][ny+1] q-paired layout for x-dominant rays
+    const float4* volY;   // [ny][nz+2][nx+1] q-paired layout for y-dominant rays
+    float2* l_out;        // FWD_LINE(_G): [V][R][K] line integrals (nullable in LINE_G)
+    float* g_out;         // FWD_LINE_G: [2][V][R][K] expected counts
+    const float* dt;      // FWD_DEAM: d~ [2][V][R][K]
+    const uint8_t* mask;  // FWD_DEAM: [V][R][K] metal trace (nullable: none)
+    const float* bowtie;  // [K] (nullable: 1)
+    float4* payload;      // FWD_DEAM: [V][R][K] (B~1, B~2, D1, D2)
+    double* partial;      // FWD_DEAM: per-block objective; FWD_MAX: per-block max; FWD_COUNT: samples
+    uint8_t* mask_out;    // FWD_MASK
+    float threshold;      // FWD_MASK
+};
+
+struct BwdArgs {
+    const float2* rays2;    // adjoint input [V][R][K][2]
+    const float4* payload;  // update input [V][R][K][4]
+    float2* img;            // adjoint output / update in-out c [nz][ny][nx]
+    const int2* slab_views; // [n_slabs] view range [lo, hi] per z-slab
+    float invZ;
+    int clamp_nonneg;
+    unsigned long long* skipped;  // update: count of unchanged (voxel, component) pairs
+};
+
+cudaError_t launch_layout(const float2* c, const float* m, int ones, float4* volX, float4* volY,
+                          int nx, int ny, int nz, cudaStream_t s);
+cudaError_t launch_forward(int mode, const Geo& G, const Spec& S, const FwdArgs& A, int n_blocks,
+                           cudaStream_t s);
+cudaError_t launch_backward(int update, const Geo& G, const BwdArgs& A, cudaStream_t s);
+cudaError_t launch_sum_partials(const double* partial, int n, double* out, int do_max, cudaStream_t s);
+cudaError_t launch_clamp_copy(const float* d, float* dt, long long n, cudaStream_t s);
+
+}  // namespace deam

@@ -1,0 +1,482 @@
+// sm_103a kernels of the MAR-DEAM hot path (arXiv 2202.00116, Sec. 2.3):
+//   * fwd_kernel   -- ray-driven Joseph projection of the two basis images
+//                     (Eq. 8 inner sum) with fused epilogues: the polyenergetic
+//                     sums of Eq. (8) for both spectra, the metal-trace
+//                     substitution (Eq. 11), the p-step ratio (Eqs. 9-10), the
+//                     per-ray c-step payload and the I-divergence (Eq. 5);
+//   * bwd_kernel   -- voxel-driven gather backprojection that recomputes the
+//                     forward weights of every candidate ray (exact transpose,
+//                     no atomics), fused with the c-step log-ratio update;
+//   * layout_kernel, reductions and the data clamp.
+// No step is a dense contraction, so no tensor cores are used: the projector is
+// bound by gather/FMA issue, the rest by HBM.
+#include <math.h>
+
+#include "deam_internal.h"
+
+namespace deam {
+
+// ex2.approx: the SFU's 2^x (documented max relative error 2^-22); the tables
+// carry mu * log2(e) so that exp(-mu.l) = 2^(-mu'.l).
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Kahan/Neumaier-style compensated accumulation of a block partial.
+__device__ __forceinline__ void kahan_add(float& sum, float& comp, float x) {
+    const float y = x - comp;
+    const float t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+}
+
+// (1 + u) ln(1 + u) - u, the I-divergence term d ln(d/g) - d + g divided by g
+// with u = (d - g) / g.  Near u = 0 the Taylor series
+// sum_{n>=2} (-1)^n u^n / (n (n-1)) avoids the cancellation of the closed form.
+__device__ __forceinline__ float idiv_phi(float u) {
+    if (u <= -1.f) return 1.f;  // d = 0: the term is g
+    if (fabsf(u) < 0.0625f) {
+        float s = -1.f / 72.f;
+        s = fmaf(s, u, 1.f / 56.f);
+        s = fmaf(s, u, -1.f / 42.f);
+        s = fmaf(s, u, 1.f / 30.f);
+        s = fmaf(s, u, -1.f / 20.f);
+        s = fmaf(s, u, 1.f / 12.f);
+        s = fmaf(s, u, -1.f / 6.f);
+        s = fmaf(s, u, 0.5f);
+        return s * u * u;
+    }
+    return fmaf(1.f + u, log1pf(u), -u);
+}
+
+// Narrow [t0, t1] to the plane indices p with lo <= a + p b < hi (conservative
+// by one plane on each side; the per-sample test decides exactly).
+__device__ __forceinline__ void clip_planes(float a, float b, float lo, float hi, float& t0, float& t1) {
+    if (fabsf(b) < 1e-12f) {
+        if (!(a >= lo - 1.f && a < hi + 1.f)) {
+            t0 = 1.f;
+            t1 = 0.f;
+        }
+        return;
+    }
+    const float r = 1.f / b;
+    const float u = (lo - a) * r, w = (hi - a) * r;
+    t0 = fmaxf(t0, fminf(u, w));
+    t1 = fminf(t1, fmaxf(u, w));
+}
+
+template <typename T>
+__device__ __forceinline__ T block_reduce(T v, bool is_max) {
+    __shared__ T red[kFwdThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const T w = __shfl_down_sync(0xffffffffu, v, o);
+        v = is_max ? (w > v ? w : v) : v + w;
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        v = red[0];
+        for (int i = 1; i < kFwdThreads / 32; ++i) v = is_max ? (red[i] > v ? red[i] : v) : v + red[i];
+    }
+    return v;
+}
+
+// Spectral sums of one ray for both spectra: g_j = sum_E I0_j q~, S_ij = sum_E
+// mu_i I0_j q~ with q~ = 2^(-mu'.l) (bowtie applied by the caller).  Bins are
+// summed in blocks of 8 in FP32, block partials are added with compensation.
+template <bool NEED_S>
+__device__ __forceinline__ void spectral_sums(const Spec& S, float l1, float l2, float& gl, float& gh,
+                                              float& s1l, float& s2l, float& s1h, float& s2h) {
+    float cgl = 0.f, cgh = 0.f, c1l = 0.f, c2l = 0.f, c1h = 0.f, c2h = 0.f;
+    gl = gh = s1l = s2l = s1h = s2h = 0.f;
+    for (int e0 = S.e_lo; e0 < S.e_hi; e0 += 8) {
+        float pgl = 0.f, pgh = 0.f, p1l = 0.f, p2l = 0.f, p1h = 0.f, p2h = 0.f;
+        const int n = min(8, S.e_hi - e0);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if (i < n) {
+                const int e = e0 + i;
+                const float ex = ex2_approx(-fmaf(S.mu1l2[e], l1, S.mu2l2[e] * l2));
+                const float ql = S.i0l[e] * ex, qh = S.i0h[e] * ex;
+                pgl += ql;
+                pgh += qh;
+                if (NEED_S) {
+                    p1l = fmaf(S.mu1[e], ql, p1l);
+                    p2l = fmaf(S.mu2[e], ql, p2l);
+                    p1h = fmaf(S.mu1[e], qh, p1h);
+                    p2h = fmaf(S.mu2[e], qh, p2h);
+                }
+            }
+        }
+        kahan_add(gl, cgl, pgl);
+        kahan_add(gh, cgh, pgh);
+        if (NEED_S) {
+            kahan_add(s1l, c1l, p1l);
+            kahan_add(s2l, c2l, p2l);
+            kahan_add(s1h, c1h, p1h);
+            kahan_add(s2h, c2h, p2h);
+        }
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kFwdThreads) fwd_kernel(const Geo G, const Spec S, const FwdArgs A) {
+    const long long nrays = (long long)G.V * G.R * G.K;
+    double red = 0.0;  // FWD_DEAM: objective of this thread's rays; FWD_MAX: max l_1
+    for (long long y = (long long)blockIdx.x * kFwdThreads + threadIdx.x; y < nrays;
+         y += (long long)gridDim.x * kFwdThreads) {
+        const int k = (int)(y % G.K);
+        const long long vr = y / G.K;
+        const int r = (int)(vr % G.R);
+        const int v = (int)(vr / G.R);
+        const float4 vw = __ldg(&G.view4[v]);
+        const float sz = __ldg(&G.view_z[v]);
+        const float2 rw = __ldg(&G.row[r]);
+        const InPlane ip = ray_inplane(G, vw, __ldg(&G.chan[k]));
+        const float az = __fmaf_rn(ip.tau0, rw.x, sz);
+        const float bz = __fmul_rn(ip.kappa, rw.x);
+        const int np = ip.axis ? G.ny : G.nx;
+        const int nq = ip.axis ? G.nx : G.ny;
+        const float4* __restrict__ vol = ip.axis ? A.volY : A.volX;
+        float t0 = 0.f, t1 = (float)(np - 1);
+        clip_planes(ip.aq, ip.bq, -1.f, (float)nq, t0, t1);
+        clip_planes(az, bz, -1.f, (float)G.nz, t0, t1);
+        int p0 = 0, p1 = -1;
+        if (t0 <= t1) {
+            p0 = max(0, (int)floorf(t0) - 1);
+            p1 = min(np - 1, (int)ceilf(t1) + 1);
+        }
+        const int rs = nq + 1;              // pairs per (plane, z) row
+        const int ps = (G.nz + 2) * rs;     // pairs per plane
+        const float fnq = (float)nq, fnz = (float)G.nz;
+        float s1 = 0.f, s2 = 0.f;
+        int nsamp = 0;
+        for (int p = p0; p <= p1; ++p) {
+            const float pf = (float)p;
+            const float fq = __fmaf_rn(pf, ip.bq, ip.aq);
+            const float fz = __fmaf_rn(pf, bz, az);
+            if (!(fq >= -1.f && fq < fnq && fz >= -1.f && fz < fnz)) continue;
+            if (MODE == FWD_COUNT) {
+                ++nsamp;
+                continue;
+            }
+            const float jq = floorf(fq), jz = floorf(fz);
+            const float wq = fq - jq, wz = fz - jz;
+            const int e = p * ps + ((int)jz + 1) * rs + ((int)jq + 1);
+            const float4 lo = __ldg(&vol[e]);       // (c(jq), c(jq+1)) at z = jz
+            const float4 hi = __ldg(&vol[e + rs]);  // same at z = jz + 1
+            const float a1 = fmaf(wq, lo.z - lo.x, lo.x), b1 = fmaf(wq, hi.z - hi.x, hi.x);
+            const float a2 = fmaf(wq, lo.w - lo.y, lo.y), b2 = fmaf(wq, hi.w - hi.y, hi.y);
+            s1 += fmaf(wz, b1 - a1, a1);
+            s2 += fmaf(wz, b2 - a2, a2);
+        }
+        const float L = __fmul_rn(ip.Lxy, rw.y);
+        const float l1 = s1 * L, l2 = s2 * L;
+
+        if (MODE == FWD_LINE) {
+            A.l_out[y] = make_float2(l1, l2);
+        } else if (MODE == FWD_MASK) {
+            A.mask_out[y] = (uint8_t)(l1 >= A.threshold);
+        } else if (MODE == FWD_MAX) {
+            red = fmax(red, (double)l1);
+        } else if (MODE == FWD_COUNT) {
+            red += (double)nsamp;
+        } else if (MODE == FWD_LINE_G) {
+            float gl, gh, a, b, c, d;
+            spectral_sums<false>(S, l1, l2, gl, gh, a, b, c, d);
+            const float bk = A.bowtie ? __ldg(&A.bowtie[k]) : 1.f;
+            if (A.l_out) A.l_out[y] = make_float2(l1, l2);
+            A.g_out[y] = gl * bk;
+            A.g_out[nrays + y] = gh * bk;
+        } else {  // FWD_DEAM
+            float gl, gh, s1l, s2l, s1h, s2h;
+            spectral_sums<true>(S, l1, l2, gl, gh, s1l, s2l, s1h, s2h);
+            const float bk = A.bowtie ? __ldg(&A.bowtie[k]) : 1.f;
+            gl *= bk; gh *= bk; s1l *= bk; s2l *= bk; s1h *= bk; s2h *= bk;
+            float4 P = make_float4(s1l + s1h, s2l + s2h, 0.f, 0.f);
+            const bool metal = A.mask != nullptr && A.mask[y] != 0;
+            if (!metal) {
+                float f = 0.f;
+                const float dl = __ldg(&A.dt[y]), dh = __ldg(&A.dt[nrays + y]);
+                if (gl > 0.f) {
+                    const float u = (dl - gl) / gl;  // r_L - 1
+                    P.z = fmaf(u, s1l, P.z);
+                    P.w = fmaf(u, s2l, P.w);
+                    f = fmaf(gl, idiv_phi(u), f);
+                } else if (dl > 0.f) {
+                    f = INFINITY;
+                }
+                if (gh > 0.f) {
+                    const float u = (dh - gh) / gh;  // r_H - 1
+                    P.z = fmaf(u, s1h, P.z);
+                    P.w = fmaf(u, s2h, P.w);
+                    f = fmaf(gh, idiv_phi(u), f);
+                } else if (dh > 0.f) {
+                    f = INFINITY;
+                }
+                red += (double)f;
+            }
+            A.payload[y] = P;
+        }
+    }
+    if (MODE == FWD_DEAM || MODE == FWD_MAX || MODE == FWD_COUNT) {
+        const double b = block_reduce<double>(red, MODE == FWD_MAX);
+        if (threadIdx.x == 0) A.partial[blockIdx.x] = b;
+    }
+}
+
+// Voxel-driven gather backprojection.  A block owns a kTileX x kTileY tile of
+// (ix, iy) columns and a z-slab of kSlab voxels; each thread owns one column
+// and keeps its kSlab accumulators in shared memory (layout [slot][thread], so a
+// warp's accesses to one slot are conflict-free).  For every view that can reach
+// the slab, the thread takes the channels whose rays can touch its column,
+// recomputes those rays' Joseph samples at its plane with the forward kernel's
+// exact arithmetic, and for every row whose sample falls in the slab adds
+// h(x, y) * payload(y) to the two voxels the sample interpolates.
+template <int UPDATE>
+__global__ void __launch_bounds__(kTileX* kTileY) bwd_kernel(const Geo G, const BwdArgs A) {
+    __shared__ float4 acc[kSlab * kTileX * kTileY];
+    constexpr int NT = kTileX * kTileY;
+    const int tid = threadIdx.x;
+    const int ntx = (G.nx + kTileX - 1) / kTileX, nty = (G.ny + kTileY - 1) / kTileY;
+    int b = blockIdx.x;
+    const int bx = b % ntx;
+    b /= ntx;
+    const int by = b % nty;
+    const int slab = b / nty;
+    const int ix = bx * kTileX + (tid % kTileX);
+    const int iy = by * kTileY + (tid / kTileX);
+    if (ix >= G.nx || iy >= G.ny) return;  // no block-wide synchronisation below
+    const int z0 = slab * kSlab;
+#pragma unroll
+    for (int s = 0; s < kSlab; ++s) acc[s * NT + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+
+    const int2 vrange = __ldg(&A.slab_views[slab]);
+    const float fix = (float)ix, fiy = (float)iy;
+    for (int v = vrange.x; v <= vrange.y; ++v) {
+        const float4 vw = __ldg(&G.view4[v]);
+        const float sz = __ldg(&G.view_z[v]);
+        // column centre seen from the source: fan angle -> candidate channels
+        const float px = (fix - vw.x) * G.dx, py = (fiy - vw.y) * G.dy;
+        const float dot = -(px * vw.z + py * vw.w);
+        const float crs = px * vw.w - py * vw.z;
+        const float uc = fmaf(atan2f(crs, dot), G.inv_dgamma, G.chan_c0);
+        const float dist = sqrtf(dot * dot + crs * crs);
+        const float hw = G.vox_reach_mm / fmaxf(dist - G.vox_reach_mm, 1.f) * G.inv_dgamma + 1.f;
+        const int k0 = max(0, (int)ceilf(fmaxf(uc - hw, -1.f)));
+        const int k1 = min(G.K - 1, (int)floorf(fminf(uc + hw, (float)G.K)));
+        for (int k = k0; k <= k1; ++k) {
+            const InPlane ip = ray_inplane(G, vw, __ldg(&G.chan[k]));
+            const int p = ip.axis ? iy : ix;
+            const int q = ip.axis ? ix : iy;
+            const float pf = (float)p;
+            const float fq = __fmaf_rn(pf, ip.bq, ip.aq);
+            const float jq = floorf(fq);
+            const float aq = fq - jq;
+            float wq;
+            if (jq == (float)q) wq = 1.f - aq;
+            else if (jq == (float)(q - 1)) wq = aq;
+            else continue;
+            if (wq == 0.f) continue;
+            int r0 = 0, r1 = G.R - 1;
+            if (G.R > 1) {
+                // fz(r) ~= sigma_z + t_p (omega0 + r domega): rows whose sample can
+                // land in [z0 - 1, z0 + kSlab)
+                const float tp = fmaf(pf, ip.kappa, ip.tau0);
+                const float slope = tp * G.domega;
+                if (fabsf(slope) > 1e-20f) {
+                    const float base = fmaf(tp, G.omega0, sz);
+                    const float ra = ((float)(z0 - 1) - base) / slope;
+                    const float rb = ((float)(z0 + kSlab) - base) / slope;
+                    const float lo = fminf(fmaxf(fminf(ra, rb), -4.f), (float)G.R + 4.f);
+                    const float hi = fminf(fmaxf(fmaxf(ra, rb), -4.f), (float)G.R + 4.f);
+                    r0 = max(0, (int)floorf(lo) - 1);
+                    r1 = min(G.R - 1, (int)ceilf(hi) + 1);
+                }
+            }
+            const float Lw = ip.Lxy;
+            for (int r = r0; r <= r1; ++r) {
+                const float2 rw = __ldg(&G.row[r]);
+                const float fz = row_fz(ip, sz, rw.x, pf);
+                const float jz = floorf(fz);
+                const float az = fz - jz;
+                const int sl = (int)jz - z0;
+                if (sl < -1 || sl >= kSlab) continue;
+                const float w = __fmul_rn(__fmul_rn(Lw, rw.y), wq);
+                const long long yi = ((long long)v * G.R + r) * G.K + k;
+                float4 P;
+                if (UPDATE) {
+                    P = __ldg(&A.payload[yi]);
+                } else {
+                    const float2 t = __ldg(&A.rays2[yi]);
+                    P = make_float4(t.x, t.y, 0.f, 0.f);
+                }
+                if (sl >= 0) {
+                    const float w0 = w * (1.f - az);
+                    float4& a = acc[sl * NT + tid];
+                    a.x = fmaf(w0, P.x, a.x);
+                    a.y = fmaf(w0, P.y, a.y);
+                    if (UPDATE) {
+                        a.z = fmaf(w0, P.z, a.z);
+                        a.w = fmaf(w0, P.w, a.w);
+                    }
+                }
+                if (sl + 1 < kSlab) {
+                    const float w1 = w * az;
+                    float4& a = acc[(sl + 1) * NT + tid];
+                    a.x = fmaf(w1, P.x, a.x);
+                    a.y = fmaf(w1, P.y, a.y);
+                    if (UPDATE) {
+                        a.z = fmaf(w1, P.z, a.z);
+                        a.w = fmaf(w1, P.w, a.w);
+                    }
+                }
+            }
+        }
+    }
+
+    unsigned long long skipped = 0;
+    for (int s = 0; s < kSlab; ++s) {
+        const int iz = z0 + s;
+        if (iz >= G.nz) break;
+        const float4 a = acc[s * NT + tid];
+        const long long vi = ((long long)iz * G.ny + iy) * G.nx + ix;
+        if (!UPDATE) {
+            A.img[vi] = make_float2(a.x, a.y);
+            continue;
+        }
+        // c-step: c_i <- c_i - (1/Z) ln(b^_i / b~_i) = c_i - (1/Z) log1p(delta_i / b~_i)
+        float2 c = A.img[vi];
+        float ratio;
+        if (a.x > 0.f && (ratio = a.z / a.x) > -1.f) {
+            c.x = fmaf(-log1pf(ratio), A.invZ, c.x);
+            if (A.clamp_nonneg) c.x = fmaxf(c.x, 0.f);
+        } else {
+            ++skipped;
+        }
+        if (a.y > 0.f && (ratio = a.w / a.y) > -1.f) {
+            c.y = fmaf(-log1pf(ratio), A.invZ, c.y);
+            if (A.clamp_nonneg) c.y = fmaxf(c.y, 0.f);
+        } else {
+            ++skipped;
+        }
+        A.img[vi] = c;
+    }
+    if (UPDATE && skipped) atomicAdd(A.skipped, skipped);
+}
+
+// Projector volume layouts.  For the dominant axis a with planes p and the
+// other transaxial axis q, element (p, zz, qq) of vol_a holds the pair
+// (c(q = qq-1, z = zz-1), c(q = qq, z = zz-1)) as a float4, with a zero border
+// (zz = 0, nz+1 and q = -1, nq), so a sample needs two aligned 16-byte loads and
+// no bounds tests.  SRC: 0 = float2 image c, 1 = float image m (second
+// component 0), 2 = the constant image (1, 0).
+template <int SRC>
+__global__ void layout_kernel(const float2* __restrict__ c, const float* __restrict__ m, float4* __restrict__ vol,
+                              int axis, int nx, int ny, int nz) {
+    const int np = axis ? ny : nx, nq = axis ? nx : ny;
+    const long long n = (long long)np * (nz + 2) * (nq + 1);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int qq = (int)(i % (nq + 1));
+        const long long t = i / (nq + 1);
+        const int iz = (int)(t % (nz + 2)) - 1;
+        const int p = (int)(t / (nz + 2));
+        float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+        if (iz >= 0 && iz < nz) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int q = qq - 1 + h;
+                if (q < 0 || q >= nq) continue;
+                const int ix = axis ? q : p, iy = axis ? p : q;
+                const long long vi = ((long long)iz * ny + iy) * nx + ix;
+                float2 val;
+                if (SRC == 0) val = c[vi];
+                else if (SRC == 1) val = make_float2(m[vi], 0.f);
+                else val = make_float2(1.f, 0.f);
+                if (h == 0) a = val; else b = val;
+            }
+        }
+        vol[i] = make_float4(a.x, a.y, b.x, b.y);
+    }
+}
+
+// Deterministic single-block reduction (fixed order) of per-block partials.
+__global__ void __launch_bounds__(256) sum_partials_kernel(const double* __restrict__ p, int n, double* out,
+                                                           int do_max) {
+    __shared__ double sh[256];
+    double v = do_max ? -INFINITY : 0.0;
+    for (int i = threadIdx.x; i < n; i += 256) v = do_max ? fmax(v, p[i]) : v + p[i];
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] = do_max ? fmax(sh[threadIdx.x], sh[threadIdx.x + s])
+                                                      : sh[threadIdx.x] + sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
+}
+
+// d~ = max(d, 0): the nonnegative substitution of the measurements (Sec. 2.1).
+__global__ void clamp_copy_kernel(const float* __restrict__ d, float* __restrict__ dt, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        dt[i] = fmaxf(d[i], 0.f);
+}
+
+static int grid_for(long long n, int threads) {
+    long long b = (n + threads - 1) / threads;
+    if (b > 152LL * 64) b = 152LL * 64;
+    return (int)(b < 1 ? 1 : b);
+}
+
+cudaError_t launch_layout(const float2* c, const float* m, int ones, float4* volX, float4* volY, int nx, int ny,
+                          int nz, cudaStream_t s) {
+    for (int axis = 0; axis < 2; ++axis) {
+        const int np = axis ? ny : nx, nq = axis ? nx : ny;
+        const long long n = (long long)np * (nz + 2) * (nq + 1);
+        float4* vol = axis ? volY : volX;
+        const int g = grid_for(n, 256);
+        if (ones) layout_kernel<2><<<g, 256, 0, s>>>(c, m, vol, axis, nx, ny, nz);
+        else if (m) layout_kernel<1><<<g, 256, 0, s>>>(c, m, vol, axis, nx, ny, nz);
+        else layout_kernel<0><<<g, 256, 0, s>>>(c, m, vol, axis, nx, ny, nz);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forward(int mode, const Geo& G, const Spec& S, const FwdArgs& A, int n_blocks, cudaStream_t s) {
+    switch (mode) {
+        case FWD_LINE: fwd_kernel<FWD_LINE><<<n_blocks, kFwdThreads, 0, s>>>(G, S, A); break;
+        case FWD_LINE_G: fwd_kernel<FWD_LINE_G><<<n_blocks, kFwdThreads, 0, s>>>(G, S, A); break;
+        case FWD_DEAM: fwd_kernel<FWD_DEAM><<<n_blocks, kFwdThreads, 0, s>>>(G, S, A); break;
+        case FWD_MASK: fwd_kernel<FWD_MASK><<<n_blocks, kFwdThreads, 0, s>>>(G, S, A); break;
+        case FWD_MAX: fwd_kernel<FWD_MAX><<<n_blocks, kFwdThreads, 0, s>>>(G, S, A); break;
+        case FWD_COUNT: fwd_kernel<FWD_COUNT><<<n_blocks, kFwdThreads, 0, s>>>(G, S, A); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_backward(int update, const Geo& G, const BwdArgs& A, cudaStream_t s) {
+    const int ntx = (G.nx + kTileX - 1) / kTileX, nty = (G.ny + kTileY - 1) / kTileY;
+    const int nsl = (G.nz + kSlab - 1) / kSlab;
+    const int blocks = ntx * nty * nsl;
+    if (update) bwd_kernel<1><<<blocks, kTileX * kTileY, 0, s>>>(G, A);
+    else bwd_kernel<0><<<blocks, kTileX * kTileY, 0, s>>>(G, A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum_partials(const double* partial, int n, double* out, int do_max, cudaStream_t s) {
+    sum_partials_kernel<<<1, 256, 0, s>>>(partial, n, out, do_max);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_clamp_copy(const float* d, float* dt, long long n, cudaStream_t s) {
+    clamp_copy_kernel<<<grid_for(n, 256), 256, 0, s>>>(d, dt, n);
+    return cudaGetLastError();
+}
+
+}  // namespace deam

@@ -1,0 +1,257 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs, element by element, plus invariants that hold at any size.
+
+Tolerances (written from the arithmetic): projections (l, g, payload sums) are
+FP32 sums of FP32 samples with compensated spectral sums, relative L2 <= 1e-5;
+images after 10 iterations relative L2 <= 1e-4; objective values relative
+1e-5.  Rays whose dominant axis is a near tie (|u_x| and |u_y| within 1e-6) are
+left out of element-wise comparisons: the two choices are both valid Joseph
+samplings and FP32/FP64 may pick differently there."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2202_00116_gb300 import build
+    build.build()
+    import oracle
+    oracle.build()
+    import paper_2202_00116_gb300 as p
+    return p
+
+
+_CACHE = {}
+
+
+def case_data(name):
+    if name not in _CACHE:
+        case = synth.make_case(name)
+        d, metal = synth.measure(case, seed=1)
+        truth, M = synth.voxelize(case)
+        mask = (metal >= case.metal_threshold).to(torch.uint8)
+        c0 = synth.initial_image(case, truth)
+        _CACHE[name] = (case, d, mask, M, c0)
+    return _CACHE[name]
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def near_tie(geo, views=None):
+    """Rays whose |cos(beta+gamma)| and |sin(beta+gamma)| agree to 1e-6."""
+    v = np.arange(geo.n_views) if views is None else np.asarray(views)
+    beta = geo.start_angle + 2 * math.pi * v / geo.views_per_rotation
+    k = np.arange(geo.n_channels)
+    gam = (k - (geo.n_channels - 1) / 2 + geo.channel_offset) * geo.channel_pitch
+    a = beta[:, None] + gam[None, :]
+    t = np.abs(np.abs(np.cos(a)) - np.abs(np.sin(a))) < 1e-6
+    return np.broadcast_to(t[:, None, :], (len(v), geo.n_rows, geo.n_channels))
+
+
+def oracle_of(case):
+    import oracle
+    return oracle.from_case(case)
+
+
+@pytest.mark.parametrize("name", ["t2d", "t3d", "c0"])
+def test_forward_line_integrals(pkg, name):
+    case, d, mask, M, c0 = case_data(name)
+    gpu = pkg.from_case(case)
+    l, g = gpu.forward(c0.cuda(), want_l=True, want_g=True)
+    O = oracle_of(case)
+    lo = O.forward(c0.double().numpy())
+    lg = l.cpu().double().numpy()
+    keep = ~near_tie(case.geo)
+    for i in range(2):
+        assert rel_l2(lg[..., i][keep], lo[..., i][keep]) < 1e-5
+    err = np.abs(lg - lo)[keep]
+    assert err.max() <= 1e-4 * np.abs(lo).max()
+    go = O.expected(lo)
+    assert rel_l2(g.cpu().double().numpy()[:, keep], go[:, keep]) < 1e-5
+
+
+@pytest.mark.parametrize("name", ["t2d", "t3d", "c0"])
+def test_backprojection_is_the_oracle_adjoint(pkg, name):
+    case, *_ = case_data(name)
+    gpu = pkg.from_case(case)
+    y = synth.random_rays(case.geo, 21).float()
+    img = gpu.backproject(y.cuda())
+    ref = oracle_of(case).adjoint(y.double().numpy())
+    ig = img.cpu().double().numpy()
+    assert rel_l2(ig, ref) < 1e-5
+    assert np.abs(ig - ref).max() <= 1e-4 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("name", ["t3d", "c1"])
+def test_adjoint_identity_on_gpu(pkg, name):
+    case = synth.make_case(name)
+    gpu = pkg.from_case(case)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(5)
+    x = torch.rand(gpu.img_shape, generator=gen, device="cuda")
+    y = torch.rand(gpu.ray_shape + (2,), generator=gen, device="cuda")
+    Ax, _ = gpu.forward(x)
+    Aty = gpu.backproject(y)
+    lhs = torch.sum(Ax.double() * y.double()).item()
+    rhs = torch.sum(x.double() * Aty.double()).item()
+    assert abs(lhs - rhs) <= 2e-6 * abs(lhs)
+
+
+@pytest.mark.parametrize("name", ["t2d", "t3d", "c0"])
+def test_ray_terms_match_oracle(pkg, name):
+    case, d, mask, M, c0 = case_data(name)
+    gpu = pkg.from_case(case)
+    gpu.set_data(d.cuda())
+    gpu.set_metal_mask(mask.cuda(), "ray")
+    pay, F = gpu.ray_terms(c0.cuda())
+    O = oracle_of(case)
+    _, _, po, fo = O.ray_model(c0.double().numpy(), d.double().numpy(), mask.numpy(), np.arange(case.geo.n_rays))
+    pg = pay.cpu().double().numpy().reshape(-1, 4)
+    keep = ~near_tie(case.geo).reshape(-1)
+    assert rel_l2(pg[keep, :2], po[keep, :2]) < 1e-5            # B~
+    assert rel_l2(pg[keep, :2] + pg[keep, 2:], po[keep, 2:]) < 1e-5  # B^ = B~ + D
+    assert rel_l2(pg[keep, 2:], po[keep, 2:] - po[keep, :2]) < 1e-4  # D directly
+    metal = mask.numpy().reshape(-1).astype(bool)
+    assert np.all(pg[metal, 2:] == 0.0)                         # Eq. 11: p = q on the trace
+    assert F == pytest.approx(fo.sum(), rel=1e-5)
+
+
+@pytest.mark.parametrize("name", ["t2d", "t3d", "c0"])
+def test_iterations_match_oracle(pkg, name):
+    case, d, mask, M, c0 = case_data(name)
+    gpu = pkg.from_case(case)
+    O = oracle_of(case)
+    Z, _ = gpu.info()
+    assert Z == pytest.approx(O.normaliser(), rel=1e-6)
+    gpu.set_data(d.cuda())
+    gpu.set_metal_mask(mask.cuda(), "ray")
+    c = c0.clone().cuda()
+    hist = gpu.iterate(c, 10)
+    c_ref, h_ref, sk_ref = O.iterate(c0.double().numpy(), d.double().numpy(), mask.numpy(), n_iter=10)
+    assert rel_l2(c.cpu().numpy(), c_ref) < 1e-4
+    np.testing.assert_allclose(hist, h_ref, rtol=1e-5)
+    assert np.all(np.diff(hist) < 0)
+    assert gpu.info()[1] == sk_ref
+
+
+def test_metal_mask_from_metal_image(pkg):
+    case, d, mask, M, c0 = case_data("c0")
+    gpu = pkg.from_case(case)
+    gpu.set_metal_mask(M.cuda(), "voxel")
+    mg = gpu.metal_mask().cpu().numpy()
+    T, mo = oracle_of(case).metal_trace(M.double().numpy(), case.metal_threshold)
+    sure = np.abs(T - case.metal_threshold) > 1e-5 * max(T.max(), 1.0)
+    assert mo.sum() > 100
+    assert np.array_equal(mg[sure], mo[sure])
+    # a host metal image gives the same mask
+    gpu.set_metal_mask(M.clone(), "voxel")
+    assert np.array_equal(gpu.metal_mask().cpu().numpy(), mg)
+
+
+def test_metal_trace_values_do_not_matter_bitwise(pkg):
+    # Eq. 11: data on the metal trace is never used, so the iterates are bitwise equal
+    case, d, mask, M, c0 = case_data("t3d")
+    gpu = pkg.from_case(case)
+    gpu.set_metal_mask(mask.cuda(), "ray")
+    out = []
+    for dd in (d, torch.where(mask.bool()[None], torch.full_like(d, 7.0e5), d)):
+        gpu.set_data(dd.cuda())
+        c = c0.clone().cuda()
+        h = gpu.iterate(c, 3)
+        out.append((c.cpu(), h))
+    assert torch.equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_deterministic_and_host_buffers(pkg):
+    case, d, mask, M, c0 = case_data("t3d")
+    gpu = pkg.from_case(case)
+    gpu.set_data(d.cuda())
+    gpu.set_metal_mask(mask.cuda(), "ray")
+    c1 = c0.clone().cuda()
+    h1 = gpu.iterate(c1, 4)
+    c2 = c0.clone().cuda()
+    h2 = gpu.iterate(c2, 4)
+    assert torch.equal(c1, c2) and np.array_equal(h1, h2)
+    # host tensors through the same entry points
+    gpu.set_data(d.clone())
+    gpu.set_metal_mask(mask.clone(), "ray")
+    ch = c0.clone()
+    hh = gpu.iterate(ch, 4)
+    assert torch.equal(ch, c1.cpu()) and np.array_equal(hh, h1)
+
+
+def test_all_rays_metal_changes_nothing(pkg):
+    case, d, mask, M, c0 = case_data("t2d")
+    gpu = pkg.from_case(case)
+    gpu.set_data(d.cuda())
+    gpu.set_metal_mask(torch.ones_like(mask).cuda(), "ray")
+    c = c0.clone().cuda()
+    hist = gpu.iterate(c, 2)
+    assert np.all(hist == 0.0)
+    assert torch.equal(c.cpu(), c0)
+
+
+def test_zero_iterations_and_errors(pkg):
+    case, d, mask, M, c0 = case_data("t2d")
+    gpu = pkg.from_case(case)
+    c = c0.clone().cuda()
+    with pytest.raises(pkg.DeamError) as e:
+        gpu.iterate(c, 1)                      # no data yet
+    assert e.value.code == pkg.DEAM_ERR_STATE
+    gpu.set_data(d.cuda())
+    assert gpu.iterate(c, 0).size == 0 and torch.equal(c.cpu(), c0)
+    with pytest.raises(ValueError):
+        gpu.iterate(c[:, :5].contiguous(), 1)  # wrong shape caught in the binding
+
+
+def test_single_voxel_closed_form_on_gpu(pkg):
+    # one voxel, one ray, one bin: c' - c* = (1 - mu.L/Z)(c - c*) with Z = (mu1+mu2) L
+    geo = synth.Geometry(1, 1, 1, 1, 2.0, 3.0, 4.0, 0.0, 0.0, 0.0, 570.0, 1040.0, 1, 8, 0.0, 0.0, 0.0,
+                         1, 1.0, 1, 0.01, 0.0, 0.0)
+    mu = np.array([[0.031], [0.013]])
+    I0 = np.array([[2e5], [2e5]])
+    gpu = pkg.Deam(geo, I0, mu)
+    L = 2.0
+    cstar = np.array([0.8, 0.3])
+    cin = np.array([1.1, 0.45])
+    dval = 2e5 * math.exp(-L * mu[:, 0] @ cstar)
+    gpu.set_data(torch.full((2, 1, 1, 1), dval, dtype=torch.float32).cuda())
+    c = torch.tensor(cin, dtype=torch.float32).reshape(1, 1, 1, 2).cuda()
+    gpu.iterate(c, 1)
+    Z = (0.031 + 0.013) * L
+    want = cin - (L / Z) * (mu[:, 0] @ (cin - cstar))
+    np.testing.assert_allclose(c.cpu().double().numpy().reshape(2), want, rtol=0, atol=2e-6)
+
+
+def test_c1_full_size_sampled_views(pkg):
+    # Full-size 256x256x32 helical case (3480 views x 16 x 672): forward on sampled
+    # views and backprojection of rays restricted to a view subset, against the
+    # oracle on those views only.
+    case = synth.make_case("c1")
+    geo = case.geo
+    gpu = pkg.from_case(case)
+    O = oracle_of(case)
+    x = synth.random_image(geo, 8).float()
+    l, _ = gpu.forward(x.cuda())
+    v0, v1 = 1700, 1712
+    lo = O.forward(x.double().numpy(), v0, v1)[v0:v1]
+    keep = ~near_tie(geo, np.arange(v0, v1))
+    assert rel_l2(l[v0:v1].cpu().double().numpy()[keep], lo[keep]) < 1e-5
+    y = torch.zeros(gpu.ray_shape + (2,))
+    gen = torch.Generator().manual_seed(9)
+    y[v0:v1] = torch.rand((v1 - v0,) + gpu.ray_shape[1:] + (2,), generator=gen)
+    img = gpu.backproject(y.cuda())
+    ref = O.adjoint(y.double().numpy(), v0, v1)
+    assert rel_l2(img.cpu().double().numpy(), ref) < 1e-5
