@@ -243,6 +243,9 @@ def run_gpu(args):
     value = world * args.steps / (ms / 1e3)
 
     # ---- end to end through the C ABI with host buffers ----
+    if args.no_e2e:
+        return finish_line(args, world, rank, pg, gpu, case, d, mask, c0, samples, ms, value, kms, kn, hist, clk,
+                           None)
     d_h = d.cpu().pin_memory()
     m_h = mask.cpu().pin_memory()
     c_h = c0.cpu().pin_memory()
@@ -262,7 +265,12 @@ def run_gpu(args):
     e2e_val = world * e2e_steps / e2e_s
     h2d = d_h.numel() * 4 + m_h.numel() + c_h.numel() * 4
     d2h = c_h.numel() * 4 + 8
+    e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+    return finish_line(args, world, rank, pg, gpu, case, d, mask, c0, samples, ms, value, kms, kn, hist, clk, e2e)
 
+
+def finish_line(args, world, rank, pg, gpu, case, d, mask, c0, samples, ms, value, kms, kn, hist, clk, e2e):
+    geo = case.geo
     # ---- roofline of the dominant kernel ----
     stages = ["layout", "forward", "reduce", "backproject"]
     avg = {s: kms[i] / max(kn[i], 1) * (2 if s == "layout" else 1) for i, s in enumerate(stages)}
@@ -299,7 +307,7 @@ def run_gpu(args):
             "stage_ms": {s: avg[s] for s in stages},
             "objective_first_last": [float(hist[0]), float(hist[-1])],
             "gpu_launches": int(sum(kn)),
-            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "e2e": e2e,
             "roofline": roofline,
             "clocks": clk.summary()}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -322,6 +330,7 @@ def main():
     ap.add_argument("--config", default="c2")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
