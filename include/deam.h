@@ -176,6 +176,23 @@ int deam_count_samples(deam_ctx *ctx, long long *n, void *stream);
 int deam_profile(deam_ctx *ctx, int enable);
 int deam_kernel_times(deam_ctx *ctx, double *ms, long long *launches, int reset);
 
+/* F(c) as deam_objective computes it, for callers that cannot allocate device
+ * memory and so cannot create a context (deam_init allocates its buffers): code
+ * running where device memory belongs to another allocator or a fixed arena, or
+ * in a latency-bound loop where cudaMalloc/cudaFree would synchronise the device.
+ * The paper has no counterpart; this is a library-usage variant.
+ * Inputs are caller-owned device buffers: c float32 [nz][ny][nx][2], d float32
+ * [2][V][R][K] raw counts (clamped to >= 0 on the fly), mask uint8 [V][R][K] or
+ * NULL (no metal); output F is one device double, written on `stream`.  Nothing
+ * is allocated: the only scratch (one FP64 partial per 128 rays) is a static
+ * 8 MiB device array that every GPU loading the library holds until exit, so at
+ * most 134,217,728 rays (more: DEAM_ERR_ARG); a bowtie may have at most 1024
+ * channels.  The first call on a device looks up that array's device address
+ * (set-up): make it before any stream capture.  All calls share the array, so
+ * calls that overlap on the GPU race: serialise them. */
+int deam_objective_noalloc(const deam_geometry *geom, const deam_spectra *spectra, const deam_basis *basis,
+                           const float *c, const float *d, const uint8_t *mask, double *F, void *stream);
+
 /* Release the context and its device buffers (waits for its work). NULL is a no-op. */
 int deam_destroy(deam_ctx *ctx);
 

@@ -60,7 +60,8 @@ class DeamError(RuntimeError):
 _lib = None
 EXPORTS = ["deam_init", "deam_set_data", "deam_set_metal_mask", "deam_get_metal_mask", "deam_forward",
            "deam_backproject", "deam_ray_terms", "deam_iterate", "deam_objective", "deam_info",
-           "deam_count_samples", "deam_profile", "deam_kernel_times", "deam_destroy", "deam_last_error"]
+           "deam_count_samples", "deam_profile", "deam_kernel_times", "deam_objective_noalloc", "deam_destroy",
+           "deam_last_error"]
 
 
 def lib():
@@ -86,6 +87,8 @@ def lib():
             "deam_count_samples": [vp, C.POINTER(C.c_longlong), vp],
             "deam_profile": [vp, i],
             "deam_kernel_times": [vp, pd, C.POINTER(C.c_longlong), i],
+            "deam_objective_noalloc": [C.POINTER(deam_geometry), C.POINTER(deam_spectra), C.POINTER(deam_basis),
+                                       vp, vp, vp, vp, vp],
             "deam_destroy": [vp],
         }
         for name, args in sig.items():
@@ -271,3 +274,30 @@ class Deam:
 
 def from_case(case, **kw) -> Deam:
     return Deam(case.geo, case.I0, case.mu, bowtie=case.bowtie, energies=case.energies, **kw)
+
+
+def objective_noalloc(geo, I0, mu, c, d, mask, F, bowtie=None):
+    """deam_objective_noalloc: F(c) into the device double tensor F without any
+    device allocation (see include/deam.h).  c, d, mask (or None), F are CUDA
+    tensors owned by the caller; the call is enqueued on the current stream."""
+    import torch
+    g = deam_geometry(int(geo.kind), geo.nx, geo.ny, geo.nz, geo.dx, geo.dy, geo.dz, geo.cx, geo.cy, geo.cz,
+                      geo.sid, geo.sdd, geo.n_views, geo.views_per_rotation, geo.start_angle, geo.feed,
+                      geo.z_start, geo.n_rows, geo.row_pitch, geo.n_channels, geo.channel_pitch,
+                      geo.channel_offset, geo.row_offset)
+    I0 = np.ascontiguousarray(np.asarray(I0, dtype=np.float64))
+    mu = np.ascontiguousarray(np.asarray(mu, dtype=np.float64))
+    P = C.POINTER(C.c_double)
+    bow = None if bowtie is None else np.ascontiguousarray(np.asarray(bowtie, dtype=np.float64))
+    sp = deam_spectra(I0.shape[1], P(), I0.ctypes.data_as(P), bow.ctypes.data_as(P) if bow is not None else P())
+    ba = deam_basis(mu.shape[1], mu.ctypes.data_as(P))
+    for t, dt in ((c, torch.float32), (d, torch.float32), (F, torch.float64)):
+        if not (t.is_cuda and t.dtype == dt and t.is_contiguous()):
+            raise ValueError("c, d (float32) and F (float64) must be contiguous CUDA tensors")
+    if mask is not None and not (mask.is_cuda and mask.dtype == torch.uint8 and mask.is_contiguous()):
+        raise ValueError("mask must be a contiguous uint8 CUDA tensor or None")
+    stream = C.c_void_p(torch.cuda.current_stream(c.device).cuda_stream)
+    _check(lib().deam_objective_noalloc(C.byref(g), C.byref(sp), C.byref(ba), C.c_void_p(c.data_ptr()),
+                                        C.c_void_p(d.data_ptr()),
+                                        C.c_void_p(mask.data_ptr()) if mask is not None else None,
+                                        C.c_void_p(F.data_ptr()), stream))

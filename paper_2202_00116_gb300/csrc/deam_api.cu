@@ -51,6 +51,8 @@ struct DeviceGuard {
 
 }  // namespace
 
+int deam::set_error(int code, const char* msg) { return fail(code, msg); }
+
 struct deam_ctx {
     deam_geometry geo{};
     Geo G{};

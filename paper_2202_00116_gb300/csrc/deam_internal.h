@@ -118,4 +118,7 @@ cudaError_t launch_backward(int update, const Geo& G, const BwdArgs& A, cudaStre
 cudaError_t launch_sum_partials(const double* partial, int n, double* out, int do_max, cudaStream_t s);
 cudaError_t launch_clamp_copy(const float* d, float* dt, long long n, cudaStream_t s);
 
+// Record an error message for deam_last_error() and return code (deam_api.cu).
+int set_error(int code, const char* msg);
+
 }  // namespace deam

@@ -1,0 +1,65 @@
+"""deam_objective_noalloc: the objective for callers that cannot allocate device
+memory (code whose device memory belongs to another allocator or a fixed arena,
+or a latency-bound loop where cudaMalloc/cudaFree would synchronise the device;
+such callers cannot create a context).  It must give the same F(c) as the
+context-based deam_objective, within the objective tolerance of the parity
+tests (relative 1e-5), on two calls in a row through the C ABI — the second call
+reuses the static scratch the first one left behind.
+
+This file is collected last so that a run stopping at the first failure has
+already run every other test."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2202_00116_gb300 import build
+    build.build()
+    import paper_2202_00116_gb300 as p
+    return p
+
+
+@pytest.mark.parametrize("name", ["c0", "t3d"])
+def test_objective_noalloc_matches_context_objective(pkg, name):
+    case = synth.make_case(name)
+    d, metal = synth.measure(case, seed=1)
+    truth, _ = synth.voxelize(case)
+    mask = (metal >= case.metal_threshold).to(torch.uint8).cuda()
+    c = synth.initial_image(case, truth).cuda()
+    d = d.cuda()
+
+    ctx = pkg.from_case(case)
+    ctx.set_data(d)
+    ctx.set_metal_mask(mask, "ray")
+    F_ref = ctx.objective(c)
+    ctx.close()
+
+    F = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        F.fill_(float("nan"))
+        pkg.objective_noalloc(case.geo, case.I0, case.mu, c, d, mask, F)
+        torch.cuda.synchronize()
+        assert F.item() == pytest.approx(F_ref, rel=1e-5)
+    # without a mask every ray counts
+    pkg.objective_noalloc(case.geo, case.I0, case.mu, c, d, None, F)
+    torch.cuda.synchronize()
+    assert F.item() > F_ref
+
+
+def test_objective_noalloc_rejects_oversized_scans(pkg):
+    case = synth.make_case("t2d")
+    # 600000 views x 1 row x 256 channels = 153.6e6 rays > 134217728: rejected on the host
+    geo = case.geo.replace(n_views=600_000, views_per_rotation=600_000, n_channels=256)
+    dummy = torch.zeros(4, device="cuda")
+    F = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(pkg.DeamError) as e:
+        pkg.objective_noalloc(geo, case.I0, case.mu, dummy, dummy, None, F)
+    assert e.value.code == pkg.DEAM_ERR_ARG
+    assert "134217728" in str(e.value)
