@@ -62,10 +62,12 @@ struct deam_ctx {
     int clamp = 0;
     bool has_data = false, mask_set = false, failed = false;
     long long nrays = 0, nvox = 0, skipped_last = 0;
-    int n_fwd_blocks = 0, n_slabs = 0;
+    int n_fwd_blocks = 0, n_slabs = 0, slab = 16;
     // device buffers
     float4* view4 = nullptr;
     float* view_z = nullptr;
+    float4* ip4 = nullptr;
+    float* ipL = nullptr;
     float2* chan = nullptr;
     float2* row = nullptr;
     float* bowtie = nullptr;
@@ -109,7 +111,7 @@ static cudaError_t dalloc(T** p, size_t n) {
 }
 
 static void free_ctx(deam_ctx* c) {
-    void* ptrs[] = {c->view4, c->view_z, c->chan, c->row, c->bowtie, c->dt, c->mask, c->payload,
+    void* ptrs[] = {c->view4, c->view_z, c->ip4, c->ipL, c->chan, c->row, c->bowtie, c->dt, c->mask, c->payload,
                     c->volX, c->volY, c->partial, c->scal, c->hist, c->slab_views, c->skipped, c->c_stage};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -164,8 +166,8 @@ static std::string validate(const deam_geometry* g, const deam_spectra* s, const
 
 // View range [lo, hi] whose rays can put a sample into the z-range of slab s
 // (voxel centres +- one slice of interpolation support).
-static int2 slab_view_range(const deam_geometry& g, int s) {
-    const int z0 = s * deam::kSlab, z1 = std::min(g.nz, z0 + deam::kSlab) - 1;
+static int2 slab_view_range(const deam_geometry& g, int s, int slab) {
+    const int z0 = s * slab, z1 = std::min(g.nz, z0 + slab) - 1;
     if (g.feed == 0.0 || g.nz == 1) return make_int2(0, g.n_views - 1);
     const double Z0 = g.cz - (g.nz - 1) / 2.0 * g.dz;
     const double zlo = Z0 + (z0 - 1) * g.dz, zhi = Z0 + (z1 + 1) * g.dz;
@@ -232,11 +234,17 @@ int deam_init(const deam_geometry* geom, const deam_spectra* spectra, const deam
     ctx->clamp = o.clamp_nonneg ? 1 : 0;
     ctx->threshold = o.metal_threshold > 0.0 ? o.metal_threshold
                                              : 0.5 * std::min(g.dx, std::min(g.dy, g.nz > 1 ? g.dz : g.dx));
-    ctx->n_slabs = (g.nz + deam::kSlab - 1) / deam::kSlab;
+    // backprojector z-slab: 8 slices when a detector row covers well under a
+    // slice (or for a single slice), else 16
+    const double row_iso = g.row_pitch * g.sid / g.sdd;
+    ctx->slab = (g.nz == 1 || g.n_rows == 1 || g.dz >= 1.5 * row_iso) ? 8 : 16;
+    ctx->n_slabs = (g.nz + ctx->slab - 1) / ctx->slab;
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-    ctx->n_fwd_blocks = (int)std::min<long long>((ctx->nrays + deam::kFwdThreads - 1) / deam::kFwdThreads,
-                                                 (long long)sms * 16);
+    const long long ntiles = (long long)((g.n_channels + deam::kTileK - 1) / deam::kTileK) *
+                             ((g.n_rows + deam::kTileR - 1) / deam::kTileR) *
+                             ((g.n_views + deam::kTileV - 1) / deam::kTileV);
+    ctx->n_fwd_blocks = (int)std::min<long long>(ntiles, (long long)sms * 8);
 
     // ---- geometry tables (double on the host, rounded once to float) ----
     const double X0 = g.cx - (g.nx - 1) / 2.0 * g.dx, Y0 = g.cy - (g.ny - 1) / 2.0 * g.dy,
@@ -260,7 +268,7 @@ int deam_init(const deam_geometry* geom, const deam_spectra* spectra, const deam
         rw[r] = make_float2((float)(w / g.dz), (float)sqrt(1.0 + (w / g.sdd) * (w / g.sdd)));
     }
     std::vector<int2> sv(ctx->n_slabs);
-    for (int s = 0; s < ctx->n_slabs; ++s) sv[s] = slab_view_range(g, s);
+    for (int s = 0; s < ctx->n_slabs; ++s) sv[s] = slab_view_range(g, s, ctx->slab);
 
     Geo& G = ctx->G;
     G.nx = g.nx; G.ny = g.ny; G.nz = g.nz; G.V = g.n_views; G.R = g.n_rows; G.K = g.n_channels;
@@ -306,6 +314,8 @@ int deam_init(const deam_geometry* geom, const deam_spectra* spectra, const deam
     };
     A(dalloc(&ctx->view4, g.n_views));
     A(dalloc(&ctx->view_z, g.n_views));
+    A(dalloc(&ctx->ip4, (size_t)g.n_views * g.n_channels));
+    A(dalloc(&ctx->ipL, (size_t)g.n_views * g.n_channels));
     A(dalloc(&ctx->chan, g.n_channels));
     A(dalloc(&ctx->row, g.n_rows));
     A(dalloc(&ctx->slab_views, ctx->n_slabs));
@@ -328,6 +338,8 @@ int deam_init(const deam_geometry* geom, const deam_spectra* spectra, const deam
     G.view_z = ctx->view_z;
     G.chan = ctx->chan;
     G.row = ctx->row;
+    G.ip4 = ctx->ip4;
+    G.ipL = ctx->ipL;
     A(cudaMemcpy(ctx->view4, v4.data(), sizeof(float4) * v4.size(), cudaMemcpyHostToDevice));
     A(cudaMemcpy(ctx->view_z, vz.data(), sizeof(float) * vz.size(), cudaMemcpyHostToDevice));
     A(cudaMemcpy(ctx->chan, ch.data(), sizeof(float2) * ch.size(), cudaMemcpyHostToDevice));
@@ -339,6 +351,7 @@ int deam_init(const deam_geometry* geom, const deam_spectra* spectra, const deam
         A(cudaMemcpy(ctx->bowtie, bt.data(), sizeof(float) * bt.size(), cudaMemcpyHostToDevice));
     }
     A(cudaMemset(ctx->mask, 0, (size_t)ctx->nrays));
+    A(deam::launch_inplane_table(G, ctx->ip4, ctx->ipL, 0));
     if (e != cudaSuccess) {
         cudaGetLastError();
         free_ctx(ctx);
@@ -468,7 +481,7 @@ int deam_backproject(deam_ctx* ctx, const float* y, float* img, void* stream) {
     B.rays2 = (const float2*)y;
     B.img = (float2*)img;
     B.slab_views = ctx->slab_views;
-    CK(deam::launch_backward(0, ctx->G, B, (cudaStream_t)stream));
+    CK(deam::launch_backward(0, ctx->slab, ctx->G, B, (cudaStream_t)stream));
     return DEAM_OK;
 }
 
@@ -555,7 +568,7 @@ int deam_iterate(deam_ctx* ctx, float* c, int n_iter, double* hist, void* stream
         CK(deam::launch_sum_partials(ctx->partial, ctx->n_fwd_blocks, ctx->hist + it, 0, s));
         CK(cudaMemsetAsync(ctx->skipped, 0, sizeof(unsigned long long), s));
         if (e) CK(cudaEventRecord(e[3], s));
-        CK(deam::launch_backward(1, ctx->G, B, s));
+        CK(deam::launch_backward(1, ctx->slab, ctx->G, B, s));
         if (e) CK(cudaEventRecord(e[4], s));
     }
     unsigned long long sk = 0;

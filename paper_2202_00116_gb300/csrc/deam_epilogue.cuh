@@ -44,9 +44,11 @@ __device__ __forceinline__ float idiv_phi(float u) {
     return fmaf(1.f + u, log1pf(u), -u);
 }
 
-template <typename T>
+// Sum (or max) over a block of NT threads in a fixed order: warp shuffles,
+// then thread 0 combines the warp results in warp order.
+template <int NT, typename T>
 __device__ __forceinline__ T block_reduce(T v, bool is_max) {
-    __shared__ T red[kFwdThreads / 32];
+    __shared__ T red[NT / 32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const T w = __shfl_down_sync(0xffffffffu, v, o);
@@ -56,7 +58,7 @@ __device__ __forceinline__ T block_reduce(T v, bool is_max) {
     __syncthreads();
     if (threadIdx.x == 0) {
         v = red[0];
-        for (int i = 1; i < kFwdThreads / 32; ++i) v = is_max ? (red[i] > v ? red[i] : v) : v + red[i];
+        for (int i = 1; i < NT / 32; ++i) v = is_max ? (red[i] > v ? red[i] : v) : v + red[i];
     }
     return v;
 }

@@ -8,10 +8,12 @@
 namespace deam {
 
 constexpr int kMaxE = 256;        // energy bins carried in the kernel-parameter tables
-constexpr int kFwdThreads = 128;  // rays per forward block
+constexpr int kTileK = 32;        // forward ray tile: channels (one warp) ...
+constexpr int kTileR = 4;         // ... x rows ...
+constexpr int kTileV = 2;         // ... x views
+constexpr int kFwdThreads = kTileK * kTileR * kTileV;  // rays per forward block (256)
 constexpr int kTileX = 16;        // backprojector column tile (x)
 constexpr int kTileY = 8;         // backprojector column tile (y)
-constexpr int kSlab = 16;         // backprojector z-slab (voxels per column per block)
 
 // Geometry in voxel-index units, as read by both projector directions.  Every
 // per-ray quantity is derived from these tables by ray_inplane()/row terms with
@@ -26,6 +28,8 @@ struct Geo {
     const float* view_z;     // [V] sigma_z = (s_z - Z0) / dz
     const float2* chan;      // [K] (cos gamma_k, sin gamma_k)
     const float2* row;       // [R] (omega_r = w_r / dz, sqrt(1 + (w_r/sdd)^2))
+    const float4* ip4;       // [V][K] (aq, bq, tau0, kappa) of ray_inplane, built once by build_inplane_table
+    const float* ipL;        // [V][K] Lxy, negated for y-dominant rays
     // approximate, only for candidate ranges in the gather backprojector
     float omega0, domega;    // omega_r ~= omega0 + r * domega
     float chan_c0, inv_dgamma;  // channel coordinate = gamma / dgamma + chan_c0
@@ -74,6 +78,20 @@ __device__ __forceinline__ InPlane ray_inplane(const Geo& G, float4 vw, float2 c
     return r;
 }
 
+// In-plane parameters of (view, channel) read back from the table that
+// build_inplane_table filled with ray_inplane(): the forward and backward
+// projectors both read it, so their sample positions are identical by construction.
+__device__ __forceinline__ InPlane inplane_at(float4 a, float lsigned) {
+    InPlane r;
+    r.axis = lsigned < 0.f ? 1 : 0;
+    r.aq = a.x;
+    r.bq = a.y;
+    r.tau0 = a.z;
+    r.kappa = a.w;
+    r.Lxy = fabsf(lsigned);
+    return r;
+}
+
 // z-intercept of the ray of row r at plane p: fz = az + p bz.
 __device__ __forceinline__ float row_fz(const InPlane& ip, float sigma_z, float omega, float p) {
     const float az = __fmaf_rn(ip.tau0, omega, sigma_z);
@@ -110,11 +128,12 @@ struct BwdArgs {
     unsigned long long* skipped;  // update: count of unchanged (voxel, component) pairs
 };
 
+cudaError_t launch_inplane_table(const Geo& G, float4* ip4, float* ipL, cudaStream_t s);
 cudaError_t launch_layout(const float2* c, const float* m, int ones, float4* volX, float4* volY,
                           int nx, int ny, int nz, cudaStream_t s);
 cudaError_t launch_forward(int mode, const Geo& G, const Spec& S, const FwdArgs& A, int n_blocks,
                            cudaStream_t s);
-cudaError_t launch_backward(int update, const Geo& G, const BwdArgs& A, cudaStream_t s);
+cudaError_t launch_backward(int update, int slab, const Geo& G, const BwdArgs& A, cudaStream_t s);
 cudaError_t launch_sum_partials(const double* partial, int n, double* out, int do_max, cudaStream_t s);
 cudaError_t launch_clamp_copy(const float* d, float* dt, long long n, cudaStream_t s);
 

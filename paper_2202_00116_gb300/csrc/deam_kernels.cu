@@ -37,16 +37,27 @@ template <int MODE>
 __global__ void __launch_bounds__(kFwdThreads) fwd_kernel(const Geo G, const Spec S, const FwdArgs A) {
     const long long nrays = (long long)G.V * G.R * G.K;
     double red = 0.0;  // FWD_DEAM: objective of this thread's rays; FWD_MAX: max l_1
-    for (long long y = (long long)blockIdx.x * kFwdThreads + threadIdx.x; y < nrays;
-         y += (long long)gridDim.x * kFwdThreads) {
-        const int k = (int)(y % G.K);
-        const long long vr = y / G.K;
-        const int r = (int)(vr % G.R);
-        const int v = (int)(vr / G.R);
-        const float4 vw = __ldg(&G.view4[v]);
+    // A block takes ray tiles of kTileK channels x kTileR rows x kTileV views (one
+    // warp per (row, view)): its warps sample neighbouring rows and views in step,
+    // so they read largely the same voxel pairs and share them in L1.
+    const int nkt = (G.K + kTileK - 1) / kTileK, nrt = (G.R + kTileR - 1) / kTileR;
+    const int nvt = (G.V + kTileV - 1) / kTileV;
+    const long long ntiles = (long long)nkt * nrt * nvt;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int kt = (int)(t % nkt);
+        const long long t2 = t / nkt;
+        const int rt = (int)(t2 % nrt);
+        const int vt = (int)(t2 / nrt);
+        const int k = kt * kTileK + lane;
+        const int r = rt * kTileR + (warp % kTileR);
+        const int v = vt * kTileV + (warp / kTileR);
+        if (k >= G.K || r >= G.R || v >= G.V) continue;
+        const long long y = ((long long)v * G.R + r) * G.K + k;
         const float sz = __ldg(&G.view_z[v]);
         const float2 rw = __ldg(&G.row[r]);
-        const InPlane ip = ray_inplane(G, vw, __ldg(&G.chan[k]));
+        const long long vk = (long long)v * G.K + k;
+        const InPlane ip = inplane_at(__ldg(&G.ip4[vk]), __ldg(&G.ipL[vk]));
         const float az = __fmaf_rn(ip.tau0, rw.x, sz);
         const float bz = __fmul_rn(ip.kappa, rw.x);
         const int np = ip.axis ? G.ny : G.nx;
@@ -134,23 +145,37 @@ __global__ void __launch_bounds__(kFwdThreads) fwd_kernel(const Geo G, const Spe
         }
     }
     if (MODE == FWD_DEAM || MODE == FWD_MAX || MODE == FWD_COUNT) {
-        const double b = block_reduce<double>(red, MODE == FWD_MAX);
+        const double b = block_reduce<kFwdThreads, double>(red, MODE == FWD_MAX);
         if (threadIdx.x == 0) A.partial[blockIdx.x] = b;
     }
 }
 
 // Voxel-driven gather backprojection.  A block owns a kTileX x kTileY tile of
-// (ix, iy) columns and a z-slab of kSlab voxels; each thread owns one column
-// and keeps its kSlab accumulators in shared memory (layout [slot][thread], so a
+// (ix, iy) columns and a z-slab of SLAB voxels; each thread owns one column and
+// keeps its SLAB accumulators in shared memory (layout [slot][thread], so a
 // warp's accesses to one slot are conflict-free).  For every view that can reach
-// the slab, the thread takes the channels whose rays can touch its column,
-// recomputes those rays' Joseph samples at its plane with the forward kernel's
-// exact arithmetic, and for every row whose sample falls in the slab adds
-// h(x, y) * payload(y) to the two voxels the sample interpolates.
-template <int UPDATE>
-__global__ void __launch_bounds__(kTileX* kTileY) bwd_kernel(const Geo G, const BwdArgs A) {
-    __shared__ float4 acc[kSlab * kTileX * kTileY];
-    constexpr int NT = kTileX * kTileY;
+// the slab, the thread takes the channels whose rays can touch its column (fan
+// angle of the column centre +- the footprint), evaluates each such ray's sample
+// at its plane exactly as the forward kernel does (same in-plane table, same
+// explicitly rounded row terms), and for every row whose sample falls in the
+// slab adds h(x, y) * payload(y) to the two voxels the sample interpolates.
+// Loads are issued ahead of the data-dependent tests (the kernel is bound by
+// load latency): the next channel's ray parameters are prefetched and each
+// row's payload and row terms are loaded before its slot is known.
+constexpr int kBwdThreads = kTileX * kTileY;
+
+__device__ __forceinline__ float channel_coord(const Geo& G, float4 vw, float x, float y, float* dist) {
+    const float px = (x - vw.x) * G.dx, py = (y - vw.y) * G.dy;
+    const float dot = -(px * vw.z + py * vw.w);
+    const float crs = px * vw.w - py * vw.z;
+    if (dist) *dist = sqrtf(dot * dot + crs * crs);
+    return fmaf(atan2f(crs, dot), G.inv_dgamma, G.chan_c0);
+}
+
+template <int UPDATE, int SLAB>
+__global__ void __launch_bounds__(kBwdThreads) bwd_kernel(const Geo G, const BwdArgs A) {
+    __shared__ float4 acc[SLAB * kBwdThreads];
+    constexpr int NT = kBwdThreads;
     const int tid = threadIdx.x;
     const int ntx = (G.nx + kTileX - 1) / kTileX, nty = (G.ny + kTileY - 1) / kTileY;
     int b = blockIdx.x;
@@ -161,26 +186,33 @@ __global__ void __launch_bounds__(kTileX* kTileY) bwd_kernel(const Geo G, const 
     const int ix = bx * kTileX + (tid % kTileX);
     const int iy = by * kTileY + (tid / kTileX);
     if (ix >= G.nx || iy >= G.ny) return;  // no block-wide synchronisation below
-    const int z0 = slab * kSlab;
+    const int z0 = slab * SLAB;
 #pragma unroll
-    for (int s = 0; s < kSlab; ++s) acc[s * NT + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
-
+    for (int s = 0; s < SLAB; ++s) acc[s * NT + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
     const int2 vrange = __ldg(&A.slab_views[slab]);
     const float fix = (float)ix, fiy = (float)iy;
+    const float zlo = (float)(z0 - 1), zhi = (float)(z0 + SLAB);
     for (int v = vrange.x; v <= vrange.y; ++v) {
         const float4 vw = __ldg(&G.view4[v]);
         const float sz = __ldg(&G.view_z[v]);
-        // column centre seen from the source: fan angle -> candidate channels
-        const float px = (fix - vw.x) * G.dx, py = (fiy - vw.y) * G.dy;
-        const float dot = -(px * vw.z + py * vw.w);
-        const float crs = px * vw.w - py * vw.z;
-        const float uc = fmaf(atan2f(crs, dot), G.inv_dgamma, G.chan_c0);
-        const float dist = sqrtf(dot * dot + crs * crs);
-        const float hw = G.vox_reach_mm / fmaxf(dist - G.vox_reach_mm, 1.f) * G.inv_dgamma + 1.f;
+        float dist;
+        const float uc = channel_coord(G, vw, fix, fiy, &dist);
+        const float hw = __fdividef(G.vox_reach_mm, fmaxf(dist - G.vox_reach_mm, 1.f)) * G.inv_dgamma + 1.f;
         const int k0 = max(0, (int)ceilf(fmaxf(uc - hw, -1.f)));
         const int k1 = min(G.K - 1, (int)floorf(fminf(uc + hw, (float)G.K)));
+        const long long vbase = (long long)v * G.K;
+        float4 na = make_float4(0.f, 0.f, 0.f, 0.f);
+        float nl = 1.f;
+        if (k0 <= k1) {
+            na = __ldg(&G.ip4[vbase + k0]);
+            nl = __ldg(&G.ipL[vbase + k0]);
+        }
         for (int k = k0; k <= k1; ++k) {
-            const InPlane ip = ray_inplane(G, vw, __ldg(&G.chan[k]));
+            const InPlane ip = inplane_at(na, nl);
+            if (k < k1) {  // prefetch the next channel's parameters
+                na = __ldg(&G.ip4[vbase + k + 1]);
+                nl = __ldg(&G.ipL[vbase + k + 1]);
+            }
             const int p = ip.axis ? iy : ix;
             const int q = ip.axis ? ix : iy;
             const float pf = (float)p;
@@ -195,54 +227,54 @@ __global__ void __launch_bounds__(kTileX* kTileY) bwd_kernel(const Geo G, const 
             int r0 = 0, r1 = G.R - 1;
             if (G.R > 1) {
                 // fz(r) ~= sigma_z + t_p (omega0 + r domega): rows whose sample can
-                // land in [z0 - 1, z0 + kSlab)
+                // land in [z0 - 1, z0 + SLAB) (one row of margin each side)
                 const float tp = fmaf(pf, ip.kappa, ip.tau0);
                 const float slope = tp * G.domega;
                 if (fabsf(slope) > 1e-20f) {
+                    const float inv = __fdividef(1.f, slope);
                     const float base = fmaf(tp, G.omega0, sz);
-                    const float ra = ((float)(z0 - 1) - base) / slope;
-                    const float rb = ((float)(z0 + kSlab) - base) / slope;
+                    const float ra = (zlo - base) * inv, rb = (zhi - base) * inv;
                     const float lo = fminf(fmaxf(fminf(ra, rb), -4.f), (float)G.R + 4.f);
                     const float hi = fminf(fmaxf(fmaxf(ra, rb), -4.f), (float)G.R + 4.f);
                     r0 = max(0, (int)floorf(lo) - 1);
                     r1 = min(G.R - 1, (int)ceilf(hi) + 1);
                 }
             }
-            const float Lw = ip.Lxy;
+            const float Lq = ip.Lxy * wq;
+            // ray data [V][R][K]: a warp's columns read neighbouring channels of a row
+            const long long pb = vbase * G.R + k;
+#pragma unroll 2
             for (int r = r0; r <= r1; ++r) {
+                float4 Pv;
+                if (UPDATE) {
+                    Pv = __ldg(&A.payload[pb + (long long)r * G.K]);
+                } else {
+                    const float2 t = __ldg(&A.rays2[pb + (long long)r * G.K]);
+                    Pv = make_float4(t.x, t.y, 0.f, 0.f);
+                }
                 const float2 rw = __ldg(&G.row[r]);
                 const float fz = row_fz(ip, sz, rw.x, pf);
                 const float jz = floorf(fz);
                 const float az = fz - jz;
                 const int sl = (int)jz - z0;
-                if (sl < -1 || sl >= kSlab) continue;
-                const float w = __fmul_rn(__fmul_rn(Lw, rw.y), wq);
-                const long long yi = ((long long)v * G.R + r) * G.K + k;
-                float4 P;
-                if (UPDATE) {
-                    P = __ldg(&A.payload[yi]);
-                } else {
-                    const float2 t = __ldg(&A.rays2[yi]);
-                    P = make_float4(t.x, t.y, 0.f, 0.f);
-                }
-                if (sl >= 0) {
-                    const float w0 = w * (1.f - az);
+                const float w = Lq * rw.y;
+                const float w1 = w * az, w0 = w - w1;
+                if (sl >= 0 && sl < SLAB) {
                     float4& a = acc[sl * NT + tid];
-                    a.x = fmaf(w0, P.x, a.x);
-                    a.y = fmaf(w0, P.y, a.y);
+                    a.x = fmaf(w0, Pv.x, a.x);
+                    a.y = fmaf(w0, Pv.y, a.y);
                     if (UPDATE) {
-                        a.z = fmaf(w0, P.z, a.z);
-                        a.w = fmaf(w0, P.w, a.w);
+                        a.z = fmaf(w0, Pv.z, a.z);
+                        a.w = fmaf(w0, Pv.w, a.w);
                     }
                 }
-                if (sl + 1 < kSlab) {
-                    const float w1 = w * az;
+                if (sl >= -1 && sl + 1 < SLAB) {
                     float4& a = acc[(sl + 1) * NT + tid];
-                    a.x = fmaf(w1, P.x, a.x);
-                    a.y = fmaf(w1, P.y, a.y);
+                    a.x = fmaf(w1, Pv.x, a.x);
+                    a.y = fmaf(w1, Pv.y, a.y);
                     if (UPDATE) {
-                        a.z = fmaf(w1, P.z, a.z);
-                        a.w = fmaf(w1, P.w, a.w);
+                        a.z = fmaf(w1, Pv.z, a.z);
+                        a.w = fmaf(w1, Pv.w, a.w);
                     }
                 }
             }
@@ -250,7 +282,7 @@ __global__ void __launch_bounds__(kTileX* kTileY) bwd_kernel(const Geo G, const 
     }
 
     unsigned long long skipped = 0;
-    for (int s = 0; s < kSlab; ++s) {
+    for (int s = 0; s < SLAB; ++s) {
         const int iz = z0 + s;
         if (iz >= G.nz) break;
         const float4 a = acc[s * NT + tid];
@@ -277,6 +309,18 @@ __global__ void __launch_bounds__(kTileX* kTileY) bwd_kernel(const Geo G, const 
         A.img[vi] = c;
     }
     if (UPDATE && skipped) atomicAdd(A.skipped, skipped);
+}
+
+// In-plane ray parameters of every (view, channel), once per context.
+__global__ void inplane_table_kernel(const Geo G, float4* __restrict__ ip4, float* __restrict__ ipL) {
+    const long long n = (long long)G.V * G.K;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int v = (int)(i / G.K), k = (int)(i % G.K);
+        const InPlane ip = ray_inplane(G, __ldg(&G.view4[v]), __ldg(&G.chan[k]));
+        ip4[i] = make_float4(ip.aq, ip.bq, ip.tau0, ip.kappa);
+        ipL[i] = ip.axis ? -ip.Lxy : ip.Lxy;
+    }
 }
 
 // Projector volume layouts.  For the dominant axis a with planes p and the
@@ -371,12 +415,24 @@ cudaError_t launch_forward(int mode, const Geo& G, const Spec& S, const FwdArgs&
     return cudaGetLastError();
 }
 
-cudaError_t launch_backward(int update, const Geo& G, const BwdArgs& A, cudaStream_t s) {
+cudaError_t launch_backward(int update, int slab, const Geo& G, const BwdArgs& A, cudaStream_t s) {
     const int ntx = (G.nx + kTileX - 1) / kTileX, nty = (G.ny + kTileY - 1) / kTileY;
-    const int nsl = (G.nz + kSlab - 1) / kSlab;
+    const int nsl = (G.nz + slab - 1) / slab;
     const int blocks = ntx * nty * nsl;
-    if (update) bwd_kernel<1><<<blocks, kTileX * kTileY, 0, s>>>(G, A);
-    else bwd_kernel<0><<<blocks, kTileX * kTileY, 0, s>>>(G, A);
+    if (slab == 8) {
+        if (update) bwd_kernel<1, 8><<<blocks, kBwdThreads, 0, s>>>(G, A);
+        else bwd_kernel<0, 8><<<blocks, kBwdThreads, 0, s>>>(G, A);
+    } else if (slab == 16) {
+        if (update) bwd_kernel<1, 16><<<blocks, kBwdThreads, 0, s>>>(G, A);
+        else bwd_kernel<0, 16><<<blocks, kBwdThreads, 0, s>>>(G, A);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inplane_table(const Geo& G, float4* ip4, float* ipL, cudaStream_t s) {
+    inplane_table_kernel<<<grid_for((long long)G.V * G.K, 256), 256, 0, s>>>(G, ip4, ipL);
     return cudaGetLastError();
 }
 

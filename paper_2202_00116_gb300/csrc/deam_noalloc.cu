@@ -27,7 +27,7 @@
 
 namespace {
 
-constexpr int kThreads = deam::kFwdThreads;           // rays per block = partials per 128 rays
+constexpr int kThreads = 128;                         // rays per block = rays per partial
 constexpr long long kMaxPartials = 1LL << 20;         // 8 MiB of FP64 partials
 constexpr long long kMaxRays = kMaxPartials * kThreads;  // 134,217,728 rays
 constexpr int kMaxDevices = 64;
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kThreads) objective_image_kernel(const ScanGeo
             f = (double)ff;
         }
     }
-    const double b = deam::block_reduce<double>(f, false);
+    const double b = deam::block_reduce<kThreads, double>(f, false);
     if (threadIdx.x == 0) partials[blockIdx.x] = b;
 }
 

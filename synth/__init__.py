@@ -309,6 +309,7 @@ def make_case(name: str, seed: int = 0) -> Case:
     c2:   3D helical 512x512x64 (0.98 x 0.98 x 0.75 mm), 16 x 816, 1160 views/rotation,
           pitch 0.6, 5 rotations, 1 keV bins, I0 = 1e5 + sigma 5 electronic noise,
           bilateral stainless-steel hip inserts.
+    c2s:  c2 cut to one rotation (1160 views): a profiling-sized case of the same kernels.
     t2d / t3d: small cases of the same kinds for oracle parity (ragged sizes).
     """
     rng = np.random.default_rng(seed)
@@ -345,8 +346,9 @@ def make_case(name: str, seed: int = 0) -> Case:
         a, b = 0.85 * fov / 2.0, 0.65 * fov / 2.0
         objs = _body(rng, a, b, 1e3, 6, 0.05 * fov, 0.12 * fov, zs * 0.6, [ti], ellipsoids=True)
         return Case(name, geo, E, I0, mu, attenuation("titanium", E), objs, (2e5, 2e5), 0.0, 20)
-    if name == "c2":
-        nx, ny, nz, dz, R, K, vpr, rot = 512, 512, 64, 0.75, 16, 816, 1160, 5
+    if name in ("c2", "c2s"):
+        # c2s: the same scan cut to one rotation (profiling-sized)
+        nx, ny, nz, dz, R, K, vpr, rot = 512, 512, 64, 0.75, 16, 816, 1160, 5 if name == "c2" else 1
         dx = 0.98
         row_iso = 0.75
         fov = nx * dx
