@@ -37,6 +37,11 @@ WORKLOAD = ("3D helical MAR-DEAM, 512x512x64 voxels x 2 components (0.98x0.98x0.
             "16x816 curved detector, 5800 views (1160/rot x 5, pitch 0.6), 2 spectra x 120 bins, "
             "bilateral steel hips, I0=1e5 + sigma 5")
 FP32_LANES_PER_SM = 128
+# DRAM bytes (read + write) per Joseph sample of one launch, from full ncu
+# captures of the same kernels on the one-rotation cut of this scan (6.48e9
+# samples per launch); traffic grows with the views, so it is scaled by the
+# sample count of the measured launch.  Valid for the kernel builds captured.
+DRAM_BYTES_PER_SAMPLE = {"bwd_kernel<1,16>": 3.114e9 / 6.484e9, "fwd_kernel<FWD_DEAM>": 4.433e9 / 6.484e9}
 
 
 def _peaks():
@@ -129,6 +134,16 @@ def dist_init(args):
         dist.init_process_group(backend=backend)
         pg = dist
     return world, rank, local, pg
+
+
+def reduce_max(pg, x, device):
+    """Max of a float over all ranks (the slowest rank's time); x itself at N = 1."""
+    if pg is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
 
 
 def cpu_oracle_rate(case, d, mask, c0, seconds=15.0, views=None):
@@ -234,12 +249,8 @@ def run_gpu(args):
         e1.record(stream)
         barrier()
     gpu.profile(False)
-    ms = e0.elapsed_time(e1)
+    ms = reduce_max(pg, e0.elapsed_time(e1), dev)
     kms, kn = gpu.kernel_times(reset=True)
-    if pg is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
     value = world * args.steps / (ms / 1e3)
 
     # ---- end to end through the C ABI with host buffers ----
@@ -257,11 +268,7 @@ def run_gpu(args):
         gpu.set_metal_mask(m_h, "ray")
         gpu.iterate(c_h, 1)      # copies c in, iterates, copies c and F out (synchronous)
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if pg is not None:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = reduce_max(pg, time.perf_counter() - t0, dev)
     e2e_val = world * e2e_steps / e2e_s
     h2d = d_h.numel() * 4 + m_h.numel() + c_h.numel() * 4
     d2h = c_h.numel() * 4 + 8
@@ -283,10 +290,14 @@ def finish_line(args, world, rank, pg, gpu, case, d, mask, c0, samples, ms, valu
     # flops) + 4 tap weights (4 flops)
     flops_per_sample = {"forward": 12.0, "backproject": 36.0}[dom]
     achieved = flops_per_sample * samples / (avg[dom] / 1e3) / 1e12
-    roofline = {"bound": "alu", "kernel": {"forward": "fwd_kernel<FWD_DEAM>", "backproject": "bwd_kernel<1>"}[dom],
+    slab = 8 if (geo.nz == 1 or geo.n_rows == 1 or geo.dz >= 1.5 * geo.row_pitch * geo.sid / geo.sdd) else 16
+    kname = {"forward": "fwd_kernel<FWD_DEAM>", "backproject": f"bwd_kernel<1,{slab}>"}[dom]
+    roofline = {"bound": "alu", "kernel": kname,
                 "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                 "peak_source": f"FP32 lanes 152 SMs x 128 x 2 flops x {sm_max:.0f} MHz (derived)",
-                "traffic": None,
+                "traffic": (DRAM_BYTES_PER_SAMPLE[kname] * samples if kname in DRAM_BYTES_PER_SAMPLE else None),
+                "traffic_note": "ncu dram__bytes_read+write per launch, scaled by Joseph samples from the "
+                                "one-rotation capture (profiles/)",
                 "ms_per_launch": avg[dom],
                 "hbm_compulsory_GBps": None}
     nvox, nrays = geo.n_voxels, geo.n_rays

@@ -159,6 +159,14 @@ int deam_iterate(deam_ctx *ctx, float *c, int n_iter, double *hist, void *stream
 /* F(c) (Eq. 5 over rays off the metal trace) into *out (host). Needs deam_set_data. */
 int deam_objective(deam_ctx *ctx, const float *c, double *out, void *stream);
 
+/* Gradient of the objective with respect to the image (derivative of Eq. 5
+ * through Eq. 8, metal-trace rays excluded): dF/dc_i(x) = b^_i(x) - b~_i(x) =
+ * sum_y h(x,y) sum_j (r_j - 1) S_ij(y), written to grad (device float32
+ * [nz][ny][nx][2], overwritten).  The per-ray terms are recomputed from c
+ * (nothing per energy bin is stored); *F (host, may be NULL) receives F(c).
+ * Needs deam_set_data.  Deterministic. */
+int deam_gradient(deam_ctx *ctx, const float *c, float *grad, double *F, void *stream);
+
 /* Normaliser Z in use, and the number of (voxel, component) pairs left unchanged
  * by the last c-step (b~ <= 0 or b^ <= 0). Either pointer may be NULL. */
 int deam_info(deam_ctx *ctx, double *Z, long long *skipped_last);

@@ -60,8 +60,8 @@ class DeamError(RuntimeError):
 _lib = None
 EXPORTS = ["deam_init", "deam_set_data", "deam_set_metal_mask", "deam_get_metal_mask", "deam_forward",
            "deam_backproject", "deam_ray_terms", "deam_iterate", "deam_objective", "deam_info",
-           "deam_count_samples", "deam_profile", "deam_kernel_times", "deam_objective_noalloc", "deam_destroy",
-           "deam_last_error"]
+           "deam_gradient", "deam_count_samples", "deam_profile", "deam_kernel_times", "deam_objective_noalloc",
+           "deam_destroy", "deam_last_error"]
 
 
 def lib():
@@ -84,6 +84,7 @@ def lib():
             "deam_iterate": [vp, vp, i, pd, vp],
             "deam_objective": [vp, vp, pd, vp],
             "deam_info": [vp, pd, C.POINTER(C.c_longlong)],
+            "deam_gradient": [vp, vp, vp, pd, vp],
             "deam_count_samples": [vp, C.POINTER(C.c_longlong), vp],
             "deam_profile": [vp, i],
             "deam_kernel_times": [vp, pd, C.POINTER(C.c_longlong), i],
@@ -237,6 +238,18 @@ class Deam:
                                     self._stream()))
         return F.value
 
+    def gradient(self, c, out=None):
+        """(dF/dc float32 [nz, ny, nx, 2], F(c)): the gradient of the objective,
+        b^ - b~, from one recomputation of the per-ray terms and one gather
+        backprojection."""
+        torch = self.torch
+        if out is None:
+            out = torch.empty(self.img_shape, dtype=torch.float32, device=self.device)
+        F = C.c_double()
+        _check(lib().deam_gradient(self._h, self._arg(c, self.img_shape, torch.float32),
+                                   self._arg(out, self.img_shape, torch.float32), C.byref(F), self._stream()))
+        return out, F.value
+
     def info(self):
         Z = C.c_double()
         sk = C.c_longlong()
@@ -301,3 +314,35 @@ def objective_noalloc(geo, I0, mu, c, d, mask, F, bowtie=None):
                                         C.c_void_p(d.data_ptr()),
                                         C.c_void_p(mask.data_ptr()) if mask is not None else None,
                                         C.c_void_p(F.data_ptr()), stream))
+
+
+def i_divergence(c, deam: Deam):
+    """F(c) (Eq. 5 over rays off the metal trace) as a float64 torch scalar that
+    autograd can differentiate with respect to the image c: the backward pass
+    calls deam_gradient (per-ray terms recomputed, not stored)."""
+    return _idiv_function().apply(c, deam)
+
+
+_IDIV = None
+
+
+def _idiv_function():
+    global _IDIV
+    if _IDIV is None:
+        import torch
+
+        class IDivergence(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, c, deam):
+                ctx.save_for_backward(c)
+                ctx.deam = deam
+                return torch.tensor(deam.objective(c.detach()), dtype=torch.float64, device=c.device)
+
+            @staticmethod
+            def backward(ctx, grad_out):
+                (c,) = ctx.saved_tensors
+                g, _ = ctx.deam.gradient(c.detach())
+                return (g * grad_out.to(g.dtype)), None
+
+        _IDIV = IDivergence
+    return _IDIV

@@ -481,7 +481,7 @@ int deam_backproject(deam_ctx* ctx, const float* y, float* img, void* stream) {
     B.rays2 = (const float2*)y;
     B.img = (float2*)img;
     B.slab_views = ctx->slab_views;
-    CK(deam::launch_backward(0, ctx->slab, ctx->G, B, (cudaStream_t)stream));
+    CK(deam::launch_backward(deam::BWD_ADJOINT, ctx->slab, ctx->G, B, (cudaStream_t)stream));
     return DEAM_OK;
 }
 
@@ -568,7 +568,7 @@ int deam_iterate(deam_ctx* ctx, float* c, int n_iter, double* hist, void* stream
         CK(deam::launch_sum_partials(ctx->partial, ctx->n_fwd_blocks, ctx->hist + it, 0, s));
         CK(cudaMemsetAsync(ctx->skipped, 0, sizeof(unsigned long long), s));
         if (e) CK(cudaEventRecord(e[3], s));
-        CK(deam::launch_backward(1, ctx->slab, ctx->G, B, s));
+        CK(deam::launch_backward(deam::BWD_UPDATE, ctx->slab, ctx->G, B, s));
         if (e) CK(cudaEventRecord(e[4], s));
     }
     unsigned long long sk = 0;
@@ -592,6 +592,29 @@ int deam_iterate(deam_ctx* ctx, float* c, int n_iter, double* hist, void* stream
     if (hist) memcpy(hist, h.data(), sizeof(double) * n_iter);
     for (double v : h)
         if (!isfinite(v)) return fail(DEAM_ERR_NUMERIC, "objective became non-finite");
+    return DEAM_OK;
+}
+
+int deam_gradient(deam_ctx* ctx, const float* c, float* grad, double* F, void* stream) {
+    CHECK_CTX(ctx);
+    if (!c || !grad) return fail(DEAM_ERR_ARG, "c and grad must not be NULL");
+    if (!ctx->has_data) return fail(DEAM_ERR_STATE, "deam_set_data has not been called");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    // per-ray terms recomputed from c (nothing per energy bin is stored), then
+    // the gather backprojection of D = sum_j (r_j - 1) S_ij gives b^ - b~
+    int rc = ray_terms(ctx, (const float2*)c, ctx->payload, nullptr, ctx->scal, s);
+    if (rc != DEAM_OK) return rc;
+    deam::BwdArgs B{};
+    B.payload = ctx->payload;
+    B.img = (float2*)grad;
+    B.slab_views = ctx->slab_views;
+    CK(deam::launch_backward(deam::BWD_GRADIENT, ctx->slab, ctx->G, B, s));
+    if (F) {
+        CK(cudaMemcpyAsync(F, ctx->scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (!isfinite(*F)) return fail(DEAM_ERR_NUMERIC, "objective is not finite");
+    }
     return DEAM_OK;
 }
 

@@ -102,6 +102,7 @@ __device__ __forceinline__ float row_fz(const InPlane& ip, float sigma_z, float 
 // ---------------------------------------------------------------------------
 // kernel launchers (deam_kernels.cu)
 // ---------------------------------------------------------------------------
+enum BwdMode { BWD_ADJOINT = 0, BWD_UPDATE = 1, BWD_GRADIENT = 2 };
 enum FwdMode { FWD_LINE = 0, FWD_LINE_G = 1, FWD_DEAM = 2, FWD_MASK = 3, FWD_MAX = 4, FWD_COUNT = 5 };
 
 struct FwdArgs {
@@ -119,9 +120,9 @@ struct FwdArgs {
 };
 
 struct BwdArgs {
-    const float2* rays2;    // adjoint input [V][R][K][2]
-    const float4* payload;  // update input [V][R][K][4]
-    float2* img;            // adjoint output / update in-out c [nz][ny][nx]
+    const float2* rays2;    // BWD_ADJOINT input [V][R][K][2]
+    const float4* payload;  // BWD_UPDATE / BWD_GRADIENT input [V][R][K][4]
+    float2* img;            // adjoint or gradient output / update in-out c [nz][ny][nx]
     const int2* slab_views; // [n_slabs] view range [lo, hi] per z-slab
     float invZ;
     int clamp_nonneg;
@@ -133,7 +134,7 @@ cudaError_t launch_layout(const float2* c, const float* m, int ones, float4* vol
                           int nx, int ny, int nz, cudaStream_t s);
 cudaError_t launch_forward(int mode, const Geo& G, const Spec& S, const FwdArgs& A, int n_blocks,
                            cudaStream_t s);
-cudaError_t launch_backward(int update, int slab, const Geo& G, const BwdArgs& A, cudaStream_t s);
+cudaError_t launch_backward(int mode, int slab, const Geo& G, const BwdArgs& A, cudaStream_t s);
 cudaError_t launch_sum_partials(const double* partial, int n, double* out, int do_max, cudaStream_t s);
 cudaError_t launch_clamp_copy(const float* d, float* dt, long long n, cudaStream_t s);
 

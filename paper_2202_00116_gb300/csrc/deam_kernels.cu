@@ -63,6 +63,10 @@ __global__ void __launch_bounds__(kFwdThreads) fwd_kernel(const Geo G, const Spe
         const int np = ip.axis ? G.ny : G.nx;
         const int nq = ip.axis ? G.nx : G.ny;
         const float4* __restrict__ vol = ip.axis ? A.volY : A.volX;
+        // the volume layouts are re-read by every ray: ask L2 to keep them
+        // (evict-last), while the per-ray streams (d~, payload) go evict-first
+        unsigned long long pol;
+        asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
         float t0 = 0.f, t1 = (float)(np - 1);
         clip_planes(ip.aq, ip.bq, -1.f, (float)nq, t0, t1);
         clip_planes(az, bz, -1.f, (float)G.nz, t0, t1);
@@ -76,20 +80,32 @@ __global__ void __launch_bounds__(kFwdThreads) fwd_kernel(const Geo G, const Spe
         const float fnq = (float)nq, fnz = (float)G.nz;
         float s1 = 0.f, s2 = 0.f;
         int nsamp = 0;
+        // the sample test is monotone in p on both axes, so the planes that pass it
+        // form one interval: shrink the conservative clip to it exactly
+        auto valid = [&](int p) {
+            const float fq = __fmaf_rn((float)p, ip.bq, ip.aq);
+            const float fz = __fmaf_rn((float)p, bz, az);
+            return fq >= -1.f && fq < fnq && fz >= -1.f && fz < fnz;
+        };
+        while (p0 <= p1 && !valid(p0)) ++p0;
+        while (p1 >= p0 && !valid(p1)) --p1;
+        if (MODE == FWD_COUNT) {
+            nsamp = max(0, p1 - p0 + 1);
+            p1 = p0 - 1;
+        }
+        // no per-sample test: the loop body is branch-free and unrolls, so the
+        // loads of several planes are in flight at once
+#pragma unroll 4
         for (int p = p0; p <= p1; ++p) {
             const float pf = (float)p;
             const float fq = __fmaf_rn(pf, ip.bq, ip.aq);
             const float fz = __fmaf_rn(pf, bz, az);
-            if (!(fq >= -1.f && fq < fnq && fz >= -1.f && fz < fnz)) continue;
-            if (MODE == FWD_COUNT) {
-                ++nsamp;
-                continue;
-            }
             const float jq = floorf(fq), jz = floorf(fz);
             const float wq = fq - jq, wz = fz - jz;
             const int e = p * ps + ((int)jz + 1) * rs + ((int)jq + 1);
-            const float4 lo = __ldg(&vol[e]);       // (c(jq), c(jq+1)) at z = jz
-            const float4 hi = __ldg(&vol[e + rs]);  // same at z = jz + 1
+            float4 lo, hi;
+            asm("ld.global.nc.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;" : "=f"(lo.x), "=f"(lo.y), "=f"(lo.z), "=f"(lo.w) : "l"(vol + e), "l"(pol));
+            asm("ld.global.nc.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;" : "=f"(hi.x), "=f"(hi.y), "=f"(hi.z), "=f"(hi.w) : "l"(vol + e + rs), "l"(pol));
             const float a1 = fmaf(wq, lo.z - lo.x, lo.x), b1 = fmaf(wq, hi.z - hi.x, hi.x);
             const float a2 = fmaf(wq, lo.w - lo.y, lo.y), b2 = fmaf(wq, hi.w - hi.y, hi.y);
             s1 += fmaf(wz, b1 - a1, a1);
@@ -122,7 +138,7 @@ __global__ void __launch_bounds__(kFwdThreads) fwd_kernel(const Geo G, const Spe
             const bool metal = A.mask != nullptr && A.mask[y] != 0;
             if (!metal) {
                 float f = 0.f;
-                const float dl = __ldg(&A.dt[y]), dh = __ldg(&A.dt[nrays + y]);
+                const float dl = __ldcs(&A.dt[y]), dh = __ldcs(&A.dt[nrays + y]);
                 if (gl > 0.f) {
                     const float u = (dl - gl) / gl;  // r_L - 1
                     P.z = fmaf(u, s1l, P.z);
@@ -141,7 +157,7 @@ __global__ void __launch_bounds__(kFwdThreads) fwd_kernel(const Geo G, const Spe
                 }
                 red += (double)f;
             }
-            A.payload[y] = P;
+            __stcs(&A.payload[y], P);
         }
     }
     if (MODE == FWD_DEAM || MODE == FWD_MAX || MODE == FWD_COUNT) {
@@ -172,8 +188,24 @@ __device__ __forceinline__ float channel_coord(const Geo& G, float4 vw, float x,
     return fmaf(atan2f(crs, dot), G.inv_dgamma, G.chan_c0);
 }
 
-template <int UPDATE, int SLAB>
+template <bool FOUR, int SLAB>
+__device__ __forceinline__ void pend_flush(float4* acc, int s, int tid, float4 x) {
+    if (s >= 0 && s < SLAB) {
+        float4& a = acc[s * kBwdThreads + tid];
+        a.x += x.x;
+        a.y += x.y;
+        if (FOUR) {
+            a.z += x.z;
+            a.w += x.w;
+        }
+    }
+}
+
+template <int MODE, int SLAB>
 __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(const Geo G, const BwdArgs A) {
+    // MODE: BWD_ADJOINT (A^T of two-component ray data), BWD_UPDATE (payload ->
+    // b~, delta -> c-step), BWD_GRADIENT (payload -> delta = b^ - b~ = dF/dc)
+    constexpr bool FOUR = MODE == BWD_UPDATE;
     __shared__ float4 acc[SLAB * kBwdThreads];
     constexpr int NT = kBwdThreads;
     const int tid = threadIdx.x;
@@ -241,16 +273,23 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(const Geo G, const Bwd
                 }
             }
             const float Lq = ip.Lxy * wq;
+            // PEND: where two or more rows fall in one slice, consecutive rows
+            // add to the same slot pair: keep it in registers (plo: slot ls,
+            // phi: slot ls + 1) and write shared memory when the slot moves on
+            constexpr bool PEND = SLAB == 8;
+            float4 plo = make_float4(0.f, 0.f, 0.f, 0.f), phi = plo;
+            int ls = -1000;
             // ray data [V][R][K]: a warp's columns read neighbouring channels of a row
             const long long pb = vbase * G.R + k;
 #pragma unroll 2
             for (int r = r0; r <= r1; ++r) {
                 float4 Pv;
-                if (UPDATE) {
-                    Pv = __ldg(&A.payload[pb + (long long)r * G.K]);
-                } else {
+                if (MODE == BWD_ADJOINT) {
                     const float2 t = __ldg(&A.rays2[pb + (long long)r * G.K]);
                     Pv = make_float4(t.x, t.y, 0.f, 0.f);
+                } else {
+                    Pv = __ldg(&A.payload[pb + (long long)r * G.K]);
+                    if (MODE == BWD_GRADIENT) Pv = make_float4(Pv.z, Pv.w, 0.f, 0.f);
                 }
                 const float2 rw = __ldg(&G.row[r]);
                 const float fz = row_fz(ip, sz, rw.x, pf);
@@ -259,24 +298,52 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(const Geo G, const Bwd
                 const int sl = (int)jz - z0;
                 const float w = Lq * rw.y;
                 const float w1 = w * az, w0 = w - w1;
-                if (sl >= 0 && sl < SLAB) {
-                    float4& a = acc[sl * NT + tid];
-                    a.x = fmaf(w0, Pv.x, a.x);
-                    a.y = fmaf(w0, Pv.y, a.y);
-                    if (UPDATE) {
-                        a.z = fmaf(w0, Pv.z, a.z);
-                        a.w = fmaf(w0, Pv.w, a.w);
+                if (!PEND) {
+                    if (sl >= 0 && sl < SLAB) {
+                        float4& a = acc[sl * NT + tid];
+                        a.x = fmaf(w0, Pv.x, a.x);
+                        a.y = fmaf(w0, Pv.y, a.y);
+                        if (FOUR) {
+                            a.z = fmaf(w0, Pv.z, a.z);
+                            a.w = fmaf(w0, Pv.w, a.w);
+                        }
                     }
-                }
-                if (sl >= -1 && sl + 1 < SLAB) {
-                    float4& a = acc[(sl + 1) * NT + tid];
-                    a.x = fmaf(w1, Pv.x, a.x);
-                    a.y = fmaf(w1, Pv.y, a.y);
-                    if (UPDATE) {
-                        a.z = fmaf(w1, Pv.z, a.z);
-                        a.w = fmaf(w1, Pv.w, a.w);
+                    if (sl >= -1 && sl + 1 < SLAB) {
+                        float4& a = acc[(sl + 1) * NT + tid];
+                        a.x = fmaf(w1, Pv.x, a.x);
+                        a.y = fmaf(w1, Pv.y, a.y);
+                        if (FOUR) {
+                            a.z = fmaf(w1, Pv.z, a.z);
+                            a.w = fmaf(w1, Pv.w, a.w);
+                        }
                     }
+                    continue;
                 }
+                if (sl != ls) {   // slots rise with r: flush the slot that is complete
+                    pend_flush<FOUR, SLAB>(acc, ls, tid, plo);
+                    if (sl == ls + 1) {
+                        plo = phi;
+                    } else {
+                        pend_flush<FOUR, SLAB>(acc, ls + 1, tid, phi);
+                        plo = make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                    phi = make_float4(0.f, 0.f, 0.f, 0.f);
+                    ls = sl;
+                }
+                plo.x = fmaf(w0, Pv.x, plo.x);
+                plo.y = fmaf(w0, Pv.y, plo.y);
+                phi.x = fmaf(w1, Pv.x, phi.x);
+                phi.y = fmaf(w1, Pv.y, phi.y);
+                if (FOUR) {
+                    plo.z = fmaf(w0, Pv.z, plo.z);
+                    plo.w = fmaf(w0, Pv.w, plo.w);
+                    phi.z = fmaf(w1, Pv.z, phi.z);
+                    phi.w = fmaf(w1, Pv.w, phi.w);
+                }
+            }
+            if (PEND) {
+                pend_flush<FOUR, SLAB>(acc, ls, tid, plo);
+                pend_flush<FOUR, SLAB>(acc, ls + 1, tid, phi);
             }
         }
     }
@@ -287,7 +354,7 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(const Geo G, const Bwd
         if (iz >= G.nz) break;
         const float4 a = acc[s * NT + tid];
         const long long vi = ((long long)iz * G.ny + iy) * G.nx + ix;
-        if (!UPDATE) {
+        if (!FOUR) {  // A^T y, or the gradient delta_i
             A.img[vi] = make_float2(a.x, a.y);
             continue;
         }
@@ -308,7 +375,7 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(const Geo G, const Bwd
         }
         A.img[vi] = c;
     }
-    if (UPDATE && skipped) atomicAdd(A.skipped, skipped);
+    if (FOUR && skipped) atomicAdd(A.skipped, skipped);
 }
 
 // In-plane ray parameters of every (view, channel), once per context.
@@ -415,19 +482,23 @@ cudaError_t launch_forward(int mode, const Geo& G, const Spec& S, const FwdArgs&
     return cudaGetLastError();
 }
 
-cudaError_t launch_backward(int update, int slab, const Geo& G, const BwdArgs& A, cudaStream_t s) {
+cudaError_t launch_backward(int mode, int slab, const Geo& G, const BwdArgs& A, cudaStream_t s) {
     const int ntx = (G.nx + kTileX - 1) / kTileX, nty = (G.ny + kTileY - 1) / kTileY;
     const int nsl = (G.nz + slab - 1) / slab;
     const int blocks = ntx * nty * nsl;
+#define DEAM_BWD(M, SL) bwd_kernel<M, SL><<<blocks, kBwdThreads, 0, s>>>(G, A)
     if (slab == 8) {
-        if (update) bwd_kernel<1, 8><<<blocks, kBwdThreads, 0, s>>>(G, A);
-        else bwd_kernel<0, 8><<<blocks, kBwdThreads, 0, s>>>(G, A);
+        if (mode == BWD_UPDATE) DEAM_BWD(BWD_UPDATE, 8);
+        else if (mode == BWD_GRADIENT) DEAM_BWD(BWD_GRADIENT, 8);
+        else DEAM_BWD(BWD_ADJOINT, 8);
     } else if (slab == 16) {
-        if (update) bwd_kernel<1, 16><<<blocks, kBwdThreads, 0, s>>>(G, A);
-        else bwd_kernel<0, 16><<<blocks, kBwdThreads, 0, s>>>(G, A);
+        if (mode == BWD_UPDATE) DEAM_BWD(BWD_UPDATE, 16);
+        else if (mode == BWD_GRADIENT) DEAM_BWD(BWD_GRADIENT, 16);
+        else DEAM_BWD(BWD_ADJOINT, 16);
     } else {
         return cudaErrorInvalidValue;
     }
+#undef DEAM_BWD
     return cudaGetLastError();
 }
 

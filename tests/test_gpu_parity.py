@@ -255,3 +255,42 @@ def test_c1_full_size_sampled_views(pkg):
     img = gpu.backproject(y.cuda())
     ref = O.adjoint(y.double().numpy(), v0, v1)
     assert rel_l2(img.cpu().double().numpy(), ref) < 1e-5
+
+
+@pytest.mark.parametrize("name", ["c0", "t3d"])
+def test_precision_report(pkg, name, record_property, capsys):
+    # Error of every output of the path against the FP64 oracle on the same
+    # inputs (FP32 sampling, compensated FP32 spectral sums, FP64 objective
+    # reduction): printed and recorded, and held to the parity tolerances.
+    case, d, mask, M, c0 = case_data(name)
+    gpu = pkg.from_case(case)
+    gpu.set_data(d.cuda())
+    gpu.set_metal_mask(mask.cuda(), "ray")
+    O = oracle_of(case)
+    keep = ~near_tie(case.geo)
+    l, g = gpu.forward(c0.cuda(), want_l=True, want_g=True)
+    lo = O.forward(c0.double().numpy())
+    go = O.expected(lo)
+    pay, F = gpu.ray_terms(c0.cuda())
+    _, _, po, fo = O.ray_model(c0.double().numpy(), d.double().numpy(), mask.numpy(), np.arange(case.geo.n_rays))
+    pg = pay.cpu().double().numpy().reshape(-1, 4)
+    k = keep.reshape(-1)
+    c = c0.clone().cuda()
+    hist = gpu.iterate(c, 10)
+    c_ref, h_ref, _ = O.iterate(c0.double().numpy(), d.double().numpy(), mask.numpy(), n_iter=10)
+    errs = {
+        "line_integrals": rel_l2(l.cpu().numpy()[keep], lo[keep]),
+        "expected_counts": rel_l2(g.cpu().numpy()[:, keep], go[:, keep]),
+        "B_tilde": rel_l2(pg[k, :2], po[k, :2]),
+        "B_hat": rel_l2(pg[k, :2] + pg[k, 2:], po[k, 2:]),
+        "objective": abs(F - fo.sum()) / fo.sum(),
+        "objective_history_max": float(np.max(np.abs(hist - h_ref) / h_ref)),
+        "image_after_10": rel_l2(c.cpu().numpy(), c_ref),
+    }
+    for key, v in errs.items():
+        record_property(f"{name}_{key}", v)
+    with capsys.disabled():
+        print(f"\nprecision vs FP64 oracle [{name}]: " + ", ".join(f"{k_}={v:.2e}" for k_, v in errs.items()))
+    assert max(errs[x] for x in ("line_integrals", "expected_counts", "B_tilde", "B_hat")) < 1e-5
+    assert errs["objective"] < 1e-5 and errs["objective_history_max"] < 1e-5
+    assert errs["image_after_10"] < 1e-4
