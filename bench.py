@@ -332,6 +332,78 @@ def finish_line(args, world, rank, pg, gpu, case, d, mask, c0, samples, ms, valu
     return 0
 
 
+def run_batch(args):
+    """Batched MAR-DEAM over seeded scans of uneven size (2D slices and 3D helical
+    slabs, 180-1160 views, 1-3 metal inserts each): one batch iteration = one
+    MAR-DEAM iteration of every scan.  The same iterations run scan by scan through
+    deam_iterate for comparison, and the two results are compared."""
+    import numpy as np
+    import torch
+
+    import paper_2202_00116_gb300 as pkg
+    import synth
+    from paper_2202_00116_gb300 import build
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    cases = synth.make_batch_cases(args.batch_scans)
+    scans, imgs = [], []
+    samples = 0
+    for case in cases:
+        d, metal = synth.measure(case, device=dev, seed=1)
+        truth, _ = synth.voxelize(case, device=dev)
+        mask = (metal >= case.metal_threshold).to(torch.uint8)
+        g = pkg.from_case(case)
+        g.set_data(d)
+        g.set_metal_mask(mask, "ray")
+        samples += g.count_samples()
+        scans.append(g)
+        imgs.append(synth.initial_image(case, truth).to(dev))
+        del d, metal, truth, mask
+    stream = torch.cuda.current_stream(dev)
+    batch = pkg.DeamBatch(scans, autotune=True)
+    cb = [c.clone() for c in imgs]
+    batch.iterate(cb, args.warmup)                  # includes the tuning and the graph capture
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        batch.iterate(cb, args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms_batch = e0.elapsed_time(e1)
+    # the same iterations scan by scan
+    cs = [c.clone() for c in imgs]
+    for g, c in zip(scans, cs):
+        g.iterate(c, args.warmup)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        for g, c in zip(scans, cs):
+            g.iterate(c, 1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1)
+    diff = max(float(torch.linalg.vector_norm((a - b).double()) / torch.linalg.vector_norm(b.double()))
+               for a, b in zip(cb, cs))
+    line = {"metric": "batched DEAM iterations/s", "value": args.steps / (ms_batch / 1e3), "unit": "it/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batch / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": f"{len(cases)} seeded scans of uneven size "
+                                                         "(2D 128^2-512^2, 3D slabs 256^2x16-512^2x48, "
+                                                         "180-1160 views/rotation, 1-3 metal inserts)",
+                                            "rays": int(sum(c.geo.n_rays for c in cases)),
+                                            "voxels": int(sum(c.geo.n_voxels for c in cases))},
+            "ray_samples_per_s": samples * args.steps / (ms_batch / 1e3),
+            "sequential_deam_iterate": {"value": args.steps / (ms_seq / 1e3), "ms_per_step": ms_seq / args.steps},
+            "speedup_vs_sequential": ms_seq / ms_batch,
+            "max_rel_l2_batched_vs_sequential": diff,
+            "tuning": batch.info(), "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    batch.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -342,7 +414,10 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiling runs)")
+    ap.add_argument("--batch-scans", type=int, default=24)
     args = ap.parse_args()
+    if args.config == "batch":
+        return run_batch(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -184,6 +184,44 @@ int deam_count_samples(deam_ctx *ctx, long long *n, void *stream);
 int deam_profile(deam_ctx *ctx, int enable);
 int deam_kernel_times(deam_ctx *ctx, double *ms, long long *launches, int reset);
 
+/* ---- Batched scans ------------------------------------------------------
+ * Many independent scans of uneven size and view count, iterated together.
+ * Each scan is a context from deam_init with deam_set_data (and optionally
+ * deam_set_metal_mask) called; contexts must outlive the batch, live on the
+ * current device, and not be used by other calls while the batch iterates.
+ * One iteration of the batch is the MAR-DEAM iteration of deam_iterate for
+ * every scan, run as one persistent forward launch and one persistent
+ * backprojection launch over the work of all scans, captured once in a CUDA
+ * graph and replayed.  With autotune = 1 the first deam_batch_iterate times the
+ * candidate ray-tile shapes (32 channels x rows x views) and backprojection
+ * shapes (z-slab depth x column tile) on scratch copies of the images and keeps
+ * the fastest, then times one iteration of that persistent plan against a plan
+ * that replays every scan's own kernels on parallel graph branches, and keeps
+ * the faster plan; results equal deam_iterate's up to FP32 summation order. */
+typedef struct deam_batch deam_batch;
+
+int deam_batch_create(deam_ctx *const *ctxs, int n, int autotune, deam_batch **out);
+
+/* n_iter iterations of every scan in place on its image c[i] (device float32
+ * [nz][ny][nx][2], one per context, in creation order).  hist (host, may be
+ * NULL) receives F(c_i^k) at hist[i * n_iter + k].  Synchronises `stream`.
+ * The graph is re-captured when the image pointers change. */
+int deam_batch_iterate(deam_batch *b, float *const *c, int n_iter, double *hist, void *stream);
+
+/* Execution plan: *plan = 0 (persistent launches over all scans) or 1 (each
+ * scan's own kernels on a graph branch of its own), plan_ms[2] = the tuning
+ * time of one captured iteration of each plan.  Chosen shapes of the
+ * persistent plan: fwd_shape[2] = (rows, views) of the forward ray tile;
+ * bwd_shapes[3][3] = (slab depth, tile x, tile y) for the slab classes 2, 8 and
+ * 16 (a scan's class follows its geometry; zeros where no scan falls in a
+ * class: each non-empty class gets its own persistent launch); fwd_ms[3],
+ * bwd_ms[6] = the tuning times of every candidate (0 if not tuned).  Any
+ * pointer may be NULL. */
+int deam_batch_info(deam_batch *b, int *plan, float *plan_ms, int *fwd_shape, int *bwd_shapes, float *fwd_ms,
+                    float *bwd_ms);
+
+int deam_batch_destroy(deam_batch *b);
+
 /* F(c) as deam_objective computes it, for callers that cannot allocate device
  * memory and so cannot create a context (deam_init allocates its buffers): code
  * running where device memory belongs to another allocator or a fixed arena, or

@@ -60,7 +60,8 @@ class DeamError(RuntimeError):
 _lib = None
 EXPORTS = ["deam_init", "deam_set_data", "deam_set_metal_mask", "deam_get_metal_mask", "deam_forward",
            "deam_backproject", "deam_ray_terms", "deam_iterate", "deam_objective", "deam_info",
-           "deam_gradient", "deam_count_samples", "deam_profile", "deam_kernel_times", "deam_objective_noalloc",
+           "deam_gradient", "deam_count_samples", "deam_profile", "deam_kernel_times", "deam_batch_create",
+           "deam_batch_iterate", "deam_batch_info", "deam_batch_destroy", "deam_objective_noalloc",
            "deam_destroy", "deam_last_error"]
 
 
@@ -90,6 +91,11 @@ def lib():
             "deam_kernel_times": [vp, pd, C.POINTER(C.c_longlong), i],
             "deam_objective_noalloc": [C.POINTER(deam_geometry), C.POINTER(deam_spectra), C.POINTER(deam_basis),
                                        vp, vp, vp, vp, vp],
+            "deam_batch_create": [C.POINTER(vp), i, i, C.POINTER(vp)],
+            "deam_batch_iterate": [vp, C.POINTER(vp), i, pd, vp],
+            "deam_batch_info": [vp, C.POINTER(C.c_int), C.POINTER(C.c_float), C.POINTER(C.c_int),
+                                C.POINTER(C.c_int), C.POINTER(C.c_float), C.POINTER(C.c_float)],
+            "deam_batch_destroy": [vp],
             "deam_destroy": [vp],
         }
         for name, args in sig.items():
@@ -314,6 +320,58 @@ def objective_noalloc(geo, I0, mu, c, d, mask, F, bowtie=None):
                                         C.c_void_p(d.data_ptr()),
                                         C.c_void_p(mask.data_ptr()) if mask is not None else None,
                                         C.c_void_p(F.data_ptr()), stream))
+
+
+class DeamBatch:
+    """Several scans (Deam contexts with data set) iterated together: one
+    persistent launch per stage over all scans, replayed from a CUDA graph,
+    tile shapes picked by timing on the first iterate (autotune=True)."""
+
+    def __init__(self, scans, autotune=True):
+        import torch
+        self.torch = torch
+        self.scans = list(scans)
+        arr = (C.c_void_p * len(self.scans))(*[s._h for s in self.scans])
+        h = C.c_void_p()
+        _check(lib().deam_batch_create(arr, len(self.scans), int(bool(autotune)), C.byref(h)))
+        self._h = h
+
+    def iterate(self, images, n_iter):
+        """n_iter iterations in place on the CUDA images (one per scan); returns
+        the objective histories as a numpy array [n_scans, n_iter]."""
+        if len(images) != len(self.scans):
+            raise ValueError("one image per scan")
+        ptrs = (C.c_void_p * len(images))(*[s._arg(c, s.img_shape, self.torch.float32)
+                                            for s, c in zip(self.scans, images)])
+        hist = np.zeros((len(images), max(n_iter, 1)), dtype=np.float64)
+        stream = self.scans[0]._stream()
+        _check(lib().deam_batch_iterate(self._h, ptrs, int(n_iter), hist.ctypes.data_as(C.POINTER(C.c_double)),
+                                        stream))
+        return hist[:, :n_iter]
+
+    def info(self):
+        plan = C.c_int()
+        pm = (C.c_float * 2)()
+        f = (C.c_int * 2)()
+        b = (C.c_int * 9)()
+        fm = (C.c_float * 3)()
+        bm = (C.c_float * 6)()
+        _check(lib().deam_batch_info(self._h, C.byref(plan), pm, f, b, fm, bm))
+        bwd = [{"slab": b[3 * c], "tile": (b[3 * c + 1], b[3 * c + 2])} for c in range(3) if b[3 * c] > 0]
+        return {"plan": ["persistent", "per-scan graph branches"][plan.value], "forward_tile": (32, f[0], f[1]),
+                "backprojection": bwd,
+                "tuning_ms": {"plans": list(pm), "forward": list(fm), "backprojection": [x for x in bm if x > 0]}}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().deam_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def i_divergence(c, deam: Deam):

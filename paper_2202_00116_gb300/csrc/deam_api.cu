@@ -9,10 +9,14 @@
 #include <vector>
 
 #include "deam.h"
+#include "deam_ctx.h"
 #include "deam_internal.h"
 
 using deam::Geo;
 using deam::Spec;
+using deam::build_layouts;
+using deam::fwd_args;
+using deam::slab_view_range;
 
 namespace {
 
@@ -53,41 +57,7 @@ struct DeviceGuard {
 
 int deam::set_error(int code, const char* msg) { return fail(code, msg); }
 
-struct deam_ctx {
-    deam_geometry geo{};
-    Geo G{};
-    Spec S{};
-    int device = 0;
-    double Z = 0.0, threshold = 0.0, mumax = 0.0;
-    int clamp = 0;
-    bool has_data = false, mask_set = false, failed = false;
-    long long nrays = 0, nvox = 0, skipped_last = 0;
-    int n_fwd_blocks = 0, n_slabs = 0, slab = 16;
-    // device buffers
-    float4* view4 = nullptr;
-    float* view_z = nullptr;
-    float4* ip4 = nullptr;
-    float* ipL = nullptr;
-    float2* chan = nullptr;
-    float2* row = nullptr;
-    float* bowtie = nullptr;
-    float* dt = nullptr;
-    uint8_t* mask = nullptr;
-    float4* payload = nullptr;
-    float4* volX = nullptr;
-    float4* volY = nullptr;
-    double* partial = nullptr;
-    double* scal = nullptr;  // [0]: last reduction result
-    double* hist = nullptr;
-    int hist_cap = 0;
-    int2* slab_views = nullptr;
-    unsigned long long* skipped = nullptr;
-    float2* c_stage = nullptr;
-    // per-kernel timing of deam_iterate (deam_profile)
-    bool prof = false;
-    double prof_ms[4] = {0, 0, 0, 0};
-    long long prof_n[4] = {0, 0, 0, 0};
-};
+
 
 #define CK(x)                                                                                  \
     do {                                                                                       \
@@ -166,7 +136,7 @@ static std::string validate(const deam_geometry* g, const deam_spectra* s, const
 
 // View range [lo, hi] whose rays can put a sample into the z-range of slab s
 // (voxel centres +- one slice of interpolation support).
-static int2 slab_view_range(const deam_geometry& g, int s, int slab) {
+int2 deam::slab_view_range(const deam_geometry& g, int s, int slab) {
     const int z0 = s * slab, z1 = std::min(g.nz, z0 + slab) - 1;
     if (g.feed == 0.0 || g.nz == 1) return make_int2(0, g.n_views - 1);
     const double Z0 = g.cz - (g.nz - 1) / 2.0 * g.dz;
@@ -194,12 +164,12 @@ static int2 slab_view_range(const deam_geometry& g, int s, int slab) {
     return make_int2((int)lo, (int)hi);
 }
 
-static int build_layouts(deam_ctx* ctx, const float2* c, const float* m, int ones, cudaStream_t s) {
+int deam::build_layouts(deam_ctx* ctx, const float2* c, const float* m, int ones, cudaStream_t s) {
     CK(deam::launch_layout(c, m, ones, ctx->volX, ctx->volY, ctx->geo.nx, ctx->geo.ny, ctx->geo.nz, s));
     return DEAM_OK;
 }
 
-static deam::FwdArgs fwd_args(deam_ctx* ctx) {
+deam::FwdArgs deam::fwd_args(deam_ctx* ctx) {
     deam::FwdArgs A{};
     A.volX = ctx->volX;
     A.volY = ctx->volY;
@@ -234,10 +204,7 @@ int deam_init(const deam_geometry* geom, const deam_spectra* spectra, const deam
     ctx->clamp = o.clamp_nonneg ? 1 : 0;
     ctx->threshold = o.metal_threshold > 0.0 ? o.metal_threshold
                                              : 0.5 * std::min(g.dx, std::min(g.dy, g.nz > 1 ? g.dz : g.dx));
-    // backprojector z-slab: 8 slices when a detector row covers well under a
-    // slice (or for a single slice), else 16
-    const double row_iso = g.row_pitch * g.sid / g.sdd;
-    ctx->slab = (g.nz == 1 || g.n_rows == 1 || g.dz >= 1.5 * row_iso) ? 8 : 16;
+    ctx->slab = deam::pick_slab(g.nz, g.n_rows, g.dz, g.row_pitch, g.sid, g.sdd);
     ctx->n_slabs = (g.nz + ctx->slab - 1) / ctx->slab;
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);

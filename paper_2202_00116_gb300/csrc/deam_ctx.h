@@ -1,0 +1,54 @@
+// The context behind the opaque deam_ctx handle, shared by the single-scan
+// entry points (deam_api.cu) and the batched ones (deam_batch.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "deam.h"
+#include "deam_internal.h"
+
+struct deam_ctx {
+    deam_geometry geo{};
+    deam::Geo G{};
+    deam::Spec S{};
+    int device = 0;
+    double Z = 0.0, threshold = 0.0, mumax = 0.0;
+    int clamp = 0;
+    bool has_data = false, mask_set = false, failed = false;
+    long long nrays = 0, nvox = 0, skipped_last = 0;
+    int n_fwd_blocks = 0, n_slabs = 0, slab = 16;
+    // device buffers
+    float4* view4 = nullptr;
+    float* view_z = nullptr;
+    float4* ip4 = nullptr;
+    float* ipL = nullptr;
+    float2* chan = nullptr;
+    float2* row = nullptr;
+    float* bowtie = nullptr;
+    float* dt = nullptr;
+    uint8_t* mask = nullptr;
+    float4* payload = nullptr;
+    float4* volX = nullptr;
+    float4* volY = nullptr;
+    double* partial = nullptr;
+    double* scal = nullptr;  // [0]: last reduction result
+    double* hist = nullptr;
+    int hist_cap = 0;
+    int2* slab_views = nullptr;
+    unsigned long long* skipped = nullptr;
+    float2* c_stage = nullptr;
+    // per-kernel timing of deam_iterate (deam_profile)
+    bool prof = false;
+    double prof_ms[4] = {0, 0, 0, 0};
+    long long prof_n[4] = {0, 0, 0, 0};
+};
+
+namespace deam {
+// View range [lo, hi] whose rays can put a sample into z-slab s of depth slab.
+int2 slab_view_range(const deam_geometry& g, int s, int slab);
+// Projector volume layouts of c (or of the metal image m, or of ones).
+int build_layouts(deam_ctx* ctx, const float2* c, const float* m, int ones, cudaStream_t s);
+// Forward-kernel arguments bound to the context's buffers.
+FwdArgs fwd_args(deam_ctx* ctx);
+}  // namespace deam

@@ -129,6 +129,41 @@ struct BwdArgs {
     unsigned long long* skipped;  // update: count of unchanged (voxel, component) pairs
 };
 
+// Batched launch over many scans (deam_batch_*): per-scan descriptors in
+// device memory and prefix sums of each scan's work items.
+struct BatchDesc {
+    int n;                      // scans
+    const Geo* geos;            // [n]
+    const Spec* specs;          // [n]
+    const FwdArgs* fargs;       // [n]
+    const BwdArgs* bargs;       // [n] (slab views for the chosen slab depth)
+    const long long* ftile_off; // [n+1] prefix sums of forward ray tiles
+    const long long* btile_off; // [n+1] prefix sums of backprojection tiles
+    double* partial;            // [ftile_off[n]] objective per forward tile
+};
+// Forward ray-tile and backprojection-tile shapes an autotuner may choose from.
+constexpr int kFwdShapes[3][2] = {{8, 1}, {4, 2}, {2, 4}};             // (rows, views) x 32 channels
+constexpr int kNumBwdShapes = 6;
+constexpr int kBwdShapes[kNumBwdShapes][3] = {{2, 16, 8}, {2, 32, 4}, {8, 16, 8},
+                                              {8, 32, 4}, {16, 16, 8}, {16, 32, 4}};  // (slab, tx, ty)
+// z-slab depth of the gather backprojection for a scan: 2 for a single slice,
+// 8 when a detector row covers at most 2/3 of a slice (several rows per slot),
+// else 16.
+inline int pick_slab(int nz, int n_rows, double dz, double row_pitch, double sid, double sdd) {
+    if (nz <= 2) return 2;
+    return (n_rows == 1 || dz >= 1.5 * row_pitch * sid / sdd) ? 8 : 16;
+}
+long long forward_tiles(int shape, const Geo& G);
+long long backward_tiles(int shape, const Geo& G);
+int forward_batch_blocks_per_sm(int shape);
+int backward_batch_blocks_per_sm(int shape);
+cudaError_t launch_forward_batch(int shape, const BatchDesc& B, int grid, cudaStream_t s);
+cudaError_t launch_backward_batch(int shape, const BatchDesc& B, int grid, cudaStream_t s);
+// out[i * stride + *counter] = sum of partial[off[i] .. off[i+1]) (fixed order)
+cudaError_t launch_sum_ranges(const double* partial, const long long* off, int n, double* out, const int* counter,
+                              int stride, cudaStream_t s);
+cudaError_t launch_counter_inc(int* counter, cudaStream_t s);
+
 cudaError_t launch_inplane_table(const Geo& G, float4* ip4, float* ipL, cudaStream_t s);
 cudaError_t launch_layout(const float2* c, const float* m, int ones, float4* volX, float4* volY,
                           int nx, int ny, int nz, cudaStream_t s);

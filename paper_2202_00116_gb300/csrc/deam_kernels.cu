@@ -33,132 +33,153 @@ __device__ __forceinline__ void clip_planes(float a, float b, float lo, float hi
     t1 = fminf(t1, fmaxf(u, w));
 }
 
+// One ray (v, r, k): Joseph projection of both components, then the MODE's
+// epilogue.  Returns the ray's share of the block reduction (objective term,
+// l_1 for FWD_MAX, sample count for FWD_COUNT; 0 otherwise).
+template <int MODE>
+__device__ __forceinline__ double fwd_ray(const Geo& G, const Spec& S, const FwdArgs& A, int v, int r, int k) {
+    const long long nrays = (long long)G.V * G.R * G.K;
+    double out = 0.0;
+    const long long y = ((long long)v * G.R + r) * G.K + k;
+    const float sz = __ldg(&G.view_z[v]);
+    const float2 rw = __ldg(&G.row[r]);
+    const long long vk = (long long)v * G.K + k;
+    const InPlane ip = inplane_at(__ldg(&G.ip4[vk]), __ldg(&G.ipL[vk]));
+    const float az = __fmaf_rn(ip.tau0, rw.x, sz);
+    const float bz = __fmul_rn(ip.kappa, rw.x);
+    const int np = ip.axis ? G.ny : G.nx;
+    const int nq = ip.axis ? G.nx : G.ny;
+    const float4* __restrict__ vol = ip.axis ? A.volY : A.volX;
+    // the volume layouts are re-read by every ray: ask L2 to keep them
+    // (evict-last), while the per-ray streams (d~, payload) go evict-first
+    unsigned long long pol;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    float t0 = 0.f, t1 = (float)(np - 1);
+    clip_planes(ip.aq, ip.bq, -1.f, (float)nq, t0, t1);
+    clip_planes(az, bz, -1.f, (float)G.nz, t0, t1);
+    int p0 = 0, p1 = -1;
+    if (t0 <= t1) {
+        p0 = max(0, (int)floorf(t0) - 1);
+        p1 = min(np - 1, (int)ceilf(t1) + 1);
+    }
+    const int rs = nq + 1;              // pairs per (plane, z) row
+    const int ps = (G.nz + 2) * rs;     // pairs per plane
+    const float fnq = (float)nq, fnz = (float)G.nz;
+    float s1 = 0.f, s2 = 0.f;
+    int nsamp = 0;
+    // the sample test is monotone in p on both axes, so the planes that pass it
+    // form one interval: shrink the conservative clip to it exactly
+    auto valid = [&](int p) {
+        const float fq = __fmaf_rn((float)p, ip.bq, ip.aq);
+        const float fz = __fmaf_rn((float)p, bz, az);
+        return fq >= -1.f && fq < fnq && fz >= -1.f && fz < fnz;
+    };
+    while (p0 <= p1 && !valid(p0)) ++p0;
+    while (p1 >= p0 && !valid(p1)) --p1;
+    if (MODE == FWD_COUNT) {
+        nsamp = max(0, p1 - p0 + 1);
+        p1 = p0 - 1;
+    }
+    // no per-sample test: the loop body is branch-free and unrolls, so the
+    // loads of several planes are in flight at once
+#pragma unroll 4
+    for (int p = p0; p <= p1; ++p) {
+        const float pf = (float)p;
+        const float fq = __fmaf_rn(pf, ip.bq, ip.aq);
+        const float fz = __fmaf_rn(pf, bz, az);
+        const float jq = floorf(fq), jz = floorf(fz);
+        const float wq = fq - jq, wz = fz - jz;
+        const int e = p * ps + ((int)jz + 1) * rs + ((int)jq + 1);
+        float4 lo, hi;
+        asm("ld.global.nc.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;" : "=f"(lo.x), "=f"(lo.y), "=f"(lo.z), "=f"(lo.w) : "l"(vol + e), "l"(pol));
+        asm("ld.global.nc.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;" : "=f"(hi.x), "=f"(hi.y), "=f"(hi.z), "=f"(hi.w) : "l"(vol + e + rs), "l"(pol));
+        const float a1 = fmaf(wq, lo.z - lo.x, lo.x), b1 = fmaf(wq, hi.z - hi.x, hi.x);
+        const float a2 = fmaf(wq, lo.w - lo.y, lo.y), b2 = fmaf(wq, hi.w - hi.y, hi.y);
+        s1 += fmaf(wz, b1 - a1, a1);
+        s2 += fmaf(wz, b2 - a2, a2);
+    }
+    const float L = __fmul_rn(ip.Lxy, rw.y);
+    const float l1 = s1 * L, l2 = s2 * L;
+
+    if (MODE == FWD_LINE) {
+        A.l_out[y] = make_float2(l1, l2);
+    } else if (MODE == FWD_MASK) {
+        A.mask_out[y] = (uint8_t)(l1 >= A.threshold);
+    } else if (MODE == FWD_MAX) {
+        out = (double)l1;
+    } else if (MODE == FWD_COUNT) {
+        out = (double)nsamp;
+    } else if (MODE == FWD_LINE_G) {
+        float gl, gh, a, b, c, d;
+        spectral_sums<false>(S, l1, l2, gl, gh, a, b, c, d);
+        const float bk = A.bowtie ? __ldg(&A.bowtie[k]) : 1.f;
+        if (A.l_out) A.l_out[y] = make_float2(l1, l2);
+        A.g_out[y] = gl * bk;
+        A.g_out[nrays + y] = gh * bk;
+    } else {  // FWD_DEAM
+        float gl, gh, s1l, s2l, s1h, s2h;
+        spectral_sums<true>(S, l1, l2, gl, gh, s1l, s2l, s1h, s2h);
+        const float bk = A.bowtie ? __ldg(&A.bowtie[k]) : 1.f;
+        gl *= bk; gh *= bk; s1l *= bk; s2l *= bk; s1h *= bk; s2h *= bk;
+        float4 P = make_float4(s1l + s1h, s2l + s2h, 0.f, 0.f);
+        const bool metal = A.mask != nullptr && A.mask[y] != 0;
+        if (!metal) {
+            float f = 0.f;
+            const float dl = __ldcs(&A.dt[y]), dh = __ldcs(&A.dt[nrays + y]);
+            if (gl > 0.f) {
+                const float u = (dl - gl) / gl;  // r_L - 1
+                P.z = fmaf(u, s1l, P.z);
+                P.w = fmaf(u, s2l, P.w);
+                f = fmaf(gl, idiv_phi(u), f);
+            } else if (dl > 0.f) {
+                f = INFINITY;
+            }
+            if (gh > 0.f) {
+                const float u = (dh - gh) / gh;  // r_H - 1
+                P.z = fmaf(u, s1h, P.z);
+                P.w = fmaf(u, s2h, P.w);
+                f = fmaf(gh, idiv_phi(u), f);
+            } else if (dh > 0.f) {
+                f = INFINITY;
+            }
+            out = (double)f;
+        }
+        __stcs(&A.payload[y], P);
+    }
+    return out;
+}
+
+// Ray tiles of 32 channels (one warp) x TR rows x TV views: the warps of a block
+// sample neighbouring rows and views in step, so they read largely the same
+// voxel pairs and share them in L1.
+template <int TR, int TV>
+__device__ __forceinline__ bool ray_of_tile(const Geo& G, long long t, int& v, int& r, int& k) {
+    const int nkt = (G.K + 31) / 32, nrt = (G.R + TR - 1) / TR;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int kt = (int)(t % nkt);
+    const long long t2 = t / nkt;
+    const int rt = (int)(t2 % nrt);
+    const int vt = (int)(t2 / nrt);
+    k = kt * 32 + lane;
+    r = rt * TR + (warp % TR);
+    v = vt * TV + (warp / TR);
+    return k < G.K && r < G.R && v < G.V;
+}
+
+template <int TR, int TV>
+__host__ __device__ __forceinline__ long long ray_tiles(const Geo& G) {
+    return (long long)((G.K + 31) / 32) * ((G.R + TR - 1) / TR) * ((G.V + TV - 1) / TV);
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(kFwdThreads) fwd_kernel(const Geo G, const Spec S, const FwdArgs A) {
-    const long long nrays = (long long)G.V * G.R * G.K;
     double red = 0.0;  // FWD_DEAM: objective of this thread's rays; FWD_MAX: max l_1
-    // A block takes ray tiles of kTileK channels x kTileR rows x kTileV views (one
-    // warp per (row, view)): its warps sample neighbouring rows and views in step,
-    // so they read largely the same voxel pairs and share them in L1.
-    const int nkt = (G.K + kTileK - 1) / kTileK, nrt = (G.R + kTileR - 1) / kTileR;
-    const int nvt = (G.V + kTileV - 1) / kTileV;
-    const long long ntiles = (long long)nkt * nrt * nvt;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long ntiles = ray_tiles<kTileR, kTileV>(G);
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int kt = (int)(t % nkt);
-        const long long t2 = t / nkt;
-        const int rt = (int)(t2 % nrt);
-        const int vt = (int)(t2 / nrt);
-        const int k = kt * kTileK + lane;
-        const int r = rt * kTileR + (warp % kTileR);
-        const int v = vt * kTileV + (warp / kTileR);
-        if (k >= G.K || r >= G.R || v >= G.V) continue;
-        const long long y = ((long long)v * G.R + r) * G.K + k;
-        const float sz = __ldg(&G.view_z[v]);
-        const float2 rw = __ldg(&G.row[r]);
-        const long long vk = (long long)v * G.K + k;
-        const InPlane ip = inplane_at(__ldg(&G.ip4[vk]), __ldg(&G.ipL[vk]));
-        const float az = __fmaf_rn(ip.tau0, rw.x, sz);
-        const float bz = __fmul_rn(ip.kappa, rw.x);
-        const int np = ip.axis ? G.ny : G.nx;
-        const int nq = ip.axis ? G.nx : G.ny;
-        const float4* __restrict__ vol = ip.axis ? A.volY : A.volX;
-        // the volume layouts are re-read by every ray: ask L2 to keep them
-        // (evict-last), while the per-ray streams (d~, payload) go evict-first
-        unsigned long long pol;
-        asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
-        float t0 = 0.f, t1 = (float)(np - 1);
-        clip_planes(ip.aq, ip.bq, -1.f, (float)nq, t0, t1);
-        clip_planes(az, bz, -1.f, (float)G.nz, t0, t1);
-        int p0 = 0, p1 = -1;
-        if (t0 <= t1) {
-            p0 = max(0, (int)floorf(t0) - 1);
-            p1 = min(np - 1, (int)ceilf(t1) + 1);
-        }
-        const int rs = nq + 1;              // pairs per (plane, z) row
-        const int ps = (G.nz + 2) * rs;     // pairs per plane
-        const float fnq = (float)nq, fnz = (float)G.nz;
-        float s1 = 0.f, s2 = 0.f;
-        int nsamp = 0;
-        // the sample test is monotone in p on both axes, so the planes that pass it
-        // form one interval: shrink the conservative clip to it exactly
-        auto valid = [&](int p) {
-            const float fq = __fmaf_rn((float)p, ip.bq, ip.aq);
-            const float fz = __fmaf_rn((float)p, bz, az);
-            return fq >= -1.f && fq < fnq && fz >= -1.f && fz < fnz;
-        };
-        while (p0 <= p1 && !valid(p0)) ++p0;
-        while (p1 >= p0 && !valid(p1)) --p1;
-        if (MODE == FWD_COUNT) {
-            nsamp = max(0, p1 - p0 + 1);
-            p1 = p0 - 1;
-        }
-        // no per-sample test: the loop body is branch-free and unrolls, so the
-        // loads of several planes are in flight at once
-#pragma unroll 4
-        for (int p = p0; p <= p1; ++p) {
-            const float pf = (float)p;
-            const float fq = __fmaf_rn(pf, ip.bq, ip.aq);
-            const float fz = __fmaf_rn(pf, bz, az);
-            const float jq = floorf(fq), jz = floorf(fz);
-            const float wq = fq - jq, wz = fz - jz;
-            const int e = p * ps + ((int)jz + 1) * rs + ((int)jq + 1);
-            float4 lo, hi;
-            asm("ld.global.nc.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;" : "=f"(lo.x), "=f"(lo.y), "=f"(lo.z), "=f"(lo.w) : "l"(vol + e), "l"(pol));
-            asm("ld.global.nc.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;" : "=f"(hi.x), "=f"(hi.y), "=f"(hi.z), "=f"(hi.w) : "l"(vol + e + rs), "l"(pol));
-            const float a1 = fmaf(wq, lo.z - lo.x, lo.x), b1 = fmaf(wq, hi.z - hi.x, hi.x);
-            const float a2 = fmaf(wq, lo.w - lo.y, lo.y), b2 = fmaf(wq, hi.w - hi.y, hi.y);
-            s1 += fmaf(wz, b1 - a1, a1);
-            s2 += fmaf(wz, b2 - a2, a2);
-        }
-        const float L = __fmul_rn(ip.Lxy, rw.y);
-        const float l1 = s1 * L, l2 = s2 * L;
-
-        if (MODE == FWD_LINE) {
-            A.l_out[y] = make_float2(l1, l2);
-        } else if (MODE == FWD_MASK) {
-            A.mask_out[y] = (uint8_t)(l1 >= A.threshold);
-        } else if (MODE == FWD_MAX) {
-            red = fmax(red, (double)l1);
-        } else if (MODE == FWD_COUNT) {
-            red += (double)nsamp;
-        } else if (MODE == FWD_LINE_G) {
-            float gl, gh, a, b, c, d;
-            spectral_sums<false>(S, l1, l2, gl, gh, a, b, c, d);
-            const float bk = A.bowtie ? __ldg(&A.bowtie[k]) : 1.f;
-            if (A.l_out) A.l_out[y] = make_float2(l1, l2);
-            A.g_out[y] = gl * bk;
-            A.g_out[nrays + y] = gh * bk;
-        } else {  // FWD_DEAM
-            float gl, gh, s1l, s2l, s1h, s2h;
-            spectral_sums<true>(S, l1, l2, gl, gh, s1l, s2l, s1h, s2h);
-            const float bk = A.bowtie ? __ldg(&A.bowtie[k]) : 1.f;
-            gl *= bk; gh *= bk; s1l *= bk; s2l *= bk; s1h *= bk; s2h *= bk;
-            float4 P = make_float4(s1l + s1h, s2l + s2h, 0.f, 0.f);
-            const bool metal = A.mask != nullptr && A.mask[y] != 0;
-            if (!metal) {
-                float f = 0.f;
-                const float dl = __ldcs(&A.dt[y]), dh = __ldcs(&A.dt[nrays + y]);
-                if (gl > 0.f) {
-                    const float u = (dl - gl) / gl;  // r_L - 1
-                    P.z = fmaf(u, s1l, P.z);
-                    P.w = fmaf(u, s2l, P.w);
-                    f = fmaf(gl, idiv_phi(u), f);
-                } else if (dl > 0.f) {
-                    f = INFINITY;
-                }
-                if (gh > 0.f) {
-                    const float u = (dh - gh) / gh;  // r_H - 1
-                    P.z = fmaf(u, s1h, P.z);
-                    P.w = fmaf(u, s2h, P.w);
-                    f = fmaf(gh, idiv_phi(u), f);
-                } else if (dh > 0.f) {
-                    f = INFINITY;
-                }
-                red += (double)f;
-            }
-            __stcs(&A.payload[y], P);
-        }
+        int v, r, k;
+        if (!ray_of_tile<kTileR, kTileV>(G, t, v, r, k)) continue;
+        const double o = fwd_ray<MODE>(G, S, A, v, r, k);
+        red = MODE == FWD_MAX ? fmax(red, o) : red + o;
     }
     if (MODE == FWD_DEAM || MODE == FWD_MAX || MODE == FWD_COUNT) {
         const double b = block_reduce<kFwdThreads, double>(red, MODE == FWD_MAX);
@@ -188,10 +209,10 @@ __device__ __forceinline__ float channel_coord(const Geo& G, float4 vw, float x,
     return fmaf(atan2f(crs, dot), G.inv_dgamma, G.chan_c0);
 }
 
-template <bool FOUR, int SLAB>
+template <bool FOUR, int SLAB, int NT>
 __device__ __forceinline__ void pend_flush(float4* acc, int s, int tid, float4 x) {
     if (s >= 0 && s < SLAB) {
-        float4& a = acc[s * kBwdThreads + tid];
+        float4& a = acc[s * NT + tid];
         a.x += x.x;
         a.y += x.y;
         if (FOUR) {
@@ -201,22 +222,16 @@ __device__ __forceinline__ void pend_flush(float4* acc, int s, int tid, float4 x
     }
 }
 
-template <int MODE, int SLAB>
-__global__ void __launch_bounds__(kBwdThreads) bwd_kernel(const Geo G, const BwdArgs A) {
+// One (column tile, z-slab) of the gather backprojection: the work of one block.
+template <int MODE, int SLAB, int TX, int TY>
+__device__ __forceinline__ void bwd_tile(const Geo& G, const BwdArgs& A, float4* acc, int bx, int by, int slab) {
     // MODE: BWD_ADJOINT (A^T of two-component ray data), BWD_UPDATE (payload ->
     // b~, delta -> c-step), BWD_GRADIENT (payload -> delta = b^ - b~ = dF/dc)
     constexpr bool FOUR = MODE == BWD_UPDATE;
-    __shared__ float4 acc[SLAB * kBwdThreads];
-    constexpr int NT = kBwdThreads;
+    constexpr int NT = TX * TY;
     const int tid = threadIdx.x;
-    const int ntx = (G.nx + kTileX - 1) / kTileX, nty = (G.ny + kTileY - 1) / kTileY;
-    int b = blockIdx.x;
-    const int bx = b % ntx;
-    b /= ntx;
-    const int by = b % nty;
-    const int slab = b / nty;
-    const int ix = bx * kTileX + (tid % kTileX);
-    const int iy = by * kTileY + (tid / kTileX);
+    const int ix = bx * TX + (tid % TX);
+    const int iy = by * TY + (tid / TX);
     if (ix >= G.nx || iy >= G.ny) return;  // no block-wide synchronisation below
     const int z0 = slab * SLAB;
 #pragma unroll
@@ -320,11 +335,11 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(const Geo G, const Bwd
                     continue;
                 }
                 if (sl != ls) {   // slots rise with r: flush the slot that is complete
-                    pend_flush<FOUR, SLAB>(acc, ls, tid, plo);
+                    pend_flush<FOUR, SLAB, NT>(acc, ls, tid, plo);
                     if (sl == ls + 1) {
                         plo = phi;
                     } else {
-                        pend_flush<FOUR, SLAB>(acc, ls + 1, tid, phi);
+                        pend_flush<FOUR, SLAB, NT>(acc, ls + 1, tid, phi);
                         plo = make_float4(0.f, 0.f, 0.f, 0.f);
                     }
                     phi = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -342,8 +357,8 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(const Geo G, const Bwd
                 }
             }
             if (PEND) {
-                pend_flush<FOUR, SLAB>(acc, ls, tid, plo);
-                pend_flush<FOUR, SLAB>(acc, ls + 1, tid, phi);
+                pend_flush<FOUR, SLAB, NT>(acc, ls, tid, plo);
+                pend_flush<FOUR, SLAB, NT>(acc, ls + 1, tid, phi);
             }
         }
     }
@@ -377,6 +392,99 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(const Geo G, const Bwd
     }
     if (FOUR && skipped) atomicAdd(A.skipped, skipped);
 }
+
+
+template <int MODE, int SLAB>
+__global__ void __launch_bounds__(kBwdThreads) bwd_kernel(const Geo G, const BwdArgs A) {
+    __shared__ float4 acc[SLAB * kBwdThreads];
+    const int ntx = (G.nx + kTileX - 1) / kTileX, nty = (G.ny + kTileY - 1) / kTileY;
+    int b = blockIdx.x;
+    const int bx = b % ntx;
+    b /= ntx;
+    const int by = b % nty;
+    bwd_tile<MODE, SLAB, kTileX, kTileY>(G, A, acc, bx, by, b / nty);
+}
+
+// ---------------------------------------------------------------------------
+// Batched kernels: one persistent launch walks the work items of many scans
+// (ray tiles for the forward pass, column tiles x slabs for the backprojection);
+// each item finds its scan by binary search in the prefix sums and runs the
+// same per-ray / per-tile code as the single-scan kernels.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int find_scan(const long long* off, int n, long long t) {
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(&off[mid]) <= t) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// The scan's geometry and arguments are staged in shared memory per work item
+// (not held in registers), so the batched kernels keep the register budget,
+// and hence the occupancy, of the single-scan kernels.
+template <int TR, int TV>
+__global__ void __launch_bounds__(kFwdThreads, 5) fwd_batch_kernel(const BatchDesc B) {
+    static_assert(32 * TR * TV == kFwdThreads, "ray tile must fill the block");
+    __shared__ Geo sG;
+    __shared__ FwdArgs sA;
+    __shared__ int si;
+    const long long total = __ldg(&B.ftile_off[B.n]);
+    for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+        __syncthreads();  // the previous item is done with sG, sA and the reduction scratch
+        if (threadIdx.x == 0) {
+            si = find_scan(B.ftile_off, B.n, t);
+            sG = B.geos[si];
+            sA = B.fargs[si];
+        }
+        __syncthreads();
+        const int i = si;
+        int v, r, k;
+        double f = 0.0;
+        if (ray_of_tile<TR, TV>(sG, t - __ldg(&B.ftile_off[i]), v, r, k))
+            f = fwd_ray<FWD_DEAM>(sG, B.specs[i], sA, v, r, k);
+        const double b = block_reduce<kFwdThreads, double>(f, false);
+        if (threadIdx.x == 0) B.partial[t] = b;  // per tile: independent of the grid
+    }
+}
+
+// (the backprojection keeps the scan's descriptors in registers: staging them
+// in shared memory was measured slower for this kernel)
+template <int SLAB, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY) bwd_batch_kernel(const BatchDesc B) {
+    __shared__ float4 acc[SLAB * TX * TY];
+    const long long total = __ldg(&B.btile_off[B.n]);
+    for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+        const int i = find_scan(B.btile_off, B.n, t);
+        const Geo G = B.geos[i];
+        const BwdArgs A = B.bargs[i];
+        long long lt = t - __ldg(&B.btile_off[i]);
+        const int ntx = (G.nx + TX - 1) / TX, nty = (G.ny + TY - 1) / TY;
+        const int bx = (int)(lt % ntx);
+        lt /= ntx;
+        const int by = (int)(lt % nty);
+        bwd_tile<BWD_UPDATE, SLAB, TX, TY>(G, A, acc, bx, by, (int)(lt / nty));
+    }
+}
+
+__global__ void __launch_bounds__(256) sum_ranges_kernel(const double* __restrict__ p, const long long* __restrict__ off,
+                                                         double* out, const int* counter, int stride) {
+    __shared__ double sh[256];
+    const int i = blockIdx.x;
+    const long long a = off[i], b = off[i + 1];
+    double v = 0.0;
+    for (long long j = a + threadIdx.x; j < b; j += 256) v += p[j];
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[(long long)i * stride + (counter ? *counter : 0)] = sh[0];
+}
+
+__global__ void counter_inc_kernel(int* c) { *c += 1; }
 
 // In-plane ray parameters of every (view, channel), once per context.
 __global__ void inplane_table_kernel(const Geo G, float4* __restrict__ ip4, float* __restrict__ ipL) {
@@ -487,7 +595,11 @@ cudaError_t launch_backward(int mode, int slab, const Geo& G, const BwdArgs& A, 
     const int nsl = (G.nz + slab - 1) / slab;
     const int blocks = ntx * nty * nsl;
 #define DEAM_BWD(M, SL) bwd_kernel<M, SL><<<blocks, kBwdThreads, 0, s>>>(G, A)
-    if (slab == 8) {
+    if (slab == 2) {
+        if (mode == BWD_UPDATE) DEAM_BWD(BWD_UPDATE, 2);
+        else if (mode == BWD_GRADIENT) DEAM_BWD(BWD_GRADIENT, 2);
+        else DEAM_BWD(BWD_ADJOINT, 2);
+    } else if (slab == 8) {
         if (mode == BWD_UPDATE) DEAM_BWD(BWD_UPDATE, 8);
         else if (mode == BWD_GRADIENT) DEAM_BWD(BWD_GRADIENT, 8);
         else DEAM_BWD(BWD_ADJOINT, 8);
@@ -499,6 +611,69 @@ cudaError_t launch_backward(int mode, int slab, const Geo& G, const BwdArgs& A, 
         return cudaErrorInvalidValue;
     }
 #undef DEAM_BWD
+    return cudaGetLastError();
+}
+
+long long forward_tiles(int shape, const Geo& G) {
+    switch (shape) {
+        case 0: return ray_tiles<8, 1>(G);
+        case 1: return ray_tiles<4, 2>(G);
+        default: return ray_tiles<2, 4>(G);
+    }
+}
+
+long long backward_tiles(int shape, const Geo& G) {
+    const int slab = kBwdShapes[shape][0], tx = kBwdShapes[shape][1], ty = kBwdShapes[shape][2];
+    return (long long)((G.nx + tx - 1) / tx) * ((G.ny + ty - 1) / ty) * ((G.nz + slab - 1) / slab);
+}
+
+int forward_batch_blocks_per_sm(int shape) {
+    int nb = 1;
+    if (shape == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fwd_batch_kernel<8, 1>, kFwdThreads, 0);
+    else if (shape == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fwd_batch_kernel<4, 2>, kFwdThreads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fwd_batch_kernel<2, 4>, kFwdThreads, 0);
+    return nb > 0 ? nb : 1;
+}
+
+#define DEAM_BWD_BATCH_SHAPES(X) \
+    X(0, 2, 16, 8) X(1, 2, 32, 4) X(2, 8, 16, 8) X(3, 8, 32, 4) X(4, 16, 16, 8) X(5, 16, 32, 4)
+
+int backward_batch_blocks_per_sm(int shape) {
+    int nb = 1;
+#define X(I, SL, TX, TY) \
+    if (shape == I) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bwd_batch_kernel<SL, TX, TY>, TX * TY, 0);
+    DEAM_BWD_BATCH_SHAPES(X)
+#undef X
+    return nb > 0 ? nb : 1;
+}
+
+cudaError_t launch_forward_batch(int shape, const BatchDesc& B, int grid, cudaStream_t s) {
+    if (shape == 0) fwd_batch_kernel<8, 1><<<grid, kFwdThreads, 0, s>>>(B);
+    else if (shape == 1) fwd_batch_kernel<4, 2><<<grid, kFwdThreads, 0, s>>>(B);
+    else if (shape == 2) fwd_batch_kernel<2, 4><<<grid, kFwdThreads, 0, s>>>(B);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_backward_batch(int shape, const BatchDesc& B, int grid, cudaStream_t s) {
+#define X(I, SL, TX, TY) \
+    if (shape == I) {    \
+        bwd_batch_kernel<SL, TX, TY><<<grid, TX * TY, 0, s>>>(B); \
+        return cudaGetLastError(); \
+    }
+    DEAM_BWD_BATCH_SHAPES(X)
+#undef X
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_sum_ranges(const double* partial, const long long* off, int n, double* out, const int* counter,
+                              int stride, cudaStream_t s) {
+    sum_ranges_kernel<<<n, 256, 0, s>>>(partial, off, out, counter, stride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_counter_inc(int* counter, cudaStream_t s) {
+    counter_inc_kernel<<<1, 1, 0, s>>>(counter);
     return cudaGetLastError();
 }
 

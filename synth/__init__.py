@@ -369,6 +369,62 @@ def make_case(name: str, seed: int = 0) -> Case:
     raise ValueError(f"unknown case {name!r}")
 
 
+def make_batch_cases(n: int = 24, seed: int = 7, small: bool = False) -> list:
+    """Seeded scans of uneven size for batched reconstruction: half 2D fan slices
+    (128^2 to 512^2 pixels), half 3D helical slabs (256^2 x 16 to 512^2 x 48
+    voxels, 16 rows), 180 to 1160 views per rotation, 1 to 3 titanium or steel
+    inserts each.  small=True scales every scan down (for parity tests)."""
+    rng = np.random.default_rng(seed)
+    cases = []
+    for i in range(n):
+        metal_name = "titanium" if rng.random() < 0.5 else "steel"
+        if i % 2 == 0:   # 2D slice
+            npx = int(rng.choice([128, 192, 256, 320, 384, 448, 512]))
+            V = int(rng.integers(180, 1161))
+            if small:
+                npx, V = max(24, npx // 8), max(24, V // 12)
+            fov = float(rng.uniform(240.0, 320.0))
+            dx = fov / npx
+            K = int(8 * round(1.6 * npx / 8))
+            geo = Geometry(FAN2D, npx, npx, 1, dx, dx, 1.0, 0.0, 0.0, 0.0, 570.0, 1040.0,
+                           V, V, float(rng.uniform(0, 6.28)), 0.0, 0.0, 1, 1.0, K,
+                           fan_pitch(fov / 2.0, 570.0, K), 0.25, 0.0)
+            E, I0, mu = _spectra(2.0, 1e5)
+            half_len = 1e3
+        else:            # 3D helical slab
+            npx = int(rng.choice([256, 384, 512]))
+            nz = int(rng.choice([16, 32, 48]))
+            vpr = int(rng.integers(180, 1161))
+            R, row_iso, dxy, dz = 16, 0.75, 0.98, float(rng.choice([0.75, 1.0, 1.5]))
+            if small:
+                npx, nz, vpr, R, dxy = max(24, npx // 8), max(6, nz // 4), max(24, vpr // 12), 4, 0.98 * 8
+                row_iso = 0.75 * 4
+            fov = npx * dxy
+            K = int(8 * round((816 if not small else 56) / 8))
+            feed = 0.8 * R * row_iso
+            rot = max(1, int(math.ceil(nz * dz / feed)))
+            V = vpr * rot
+            travel = feed * V / vpr
+            geo = Geometry(HELICAL, npx, npx, nz, dxy, dxy, dz, 0.0, 0.0, 0.0, 570.0, 1040.0,
+                           V, vpr, float(rng.uniform(0, 6.28)), feed, -travel / 2.0, R,
+                           row_iso * 1040.0 / 570.0, K, fan_pitch(fov / 2.0, 570.0, K), 0.25, 0.0)
+            E, I0, mu = _spectra(2.0, 1e5)
+            half_len = nz * dz
+        a, b = 0.42 * geo.nx * geo.dx, 0.32 * geo.ny * geo.dy
+        metals = []
+        for m in range(int(rng.integers(1, 4))):
+            for _ in range(100):
+                x, y = rng.uniform(-0.6 * a, 0.6 * a), rng.uniform(-0.6 * b, 0.6 * b)
+                rr = float(rng.uniform(2.0, 6.0))
+                if all(math.hypot(x - o.centre[0], y - o.centre[1]) > rr + o.axes[0] + 3 for o in metals):
+                    metals.append(Obj("cylinder", (x, y, 0.0), (rr, rr, half_len), 0.0, metal=1.0))
+                    break
+        objs = _body(rng, a, b, half_len, 4, 0.06 * a, 0.15 * a, 0.3 * half_len if geo.nz > 1 else 0.0,
+                     metals, ellipsoids=geo.nz > 1)
+        cases.append(Case(f"batch{i}", geo, E, I0, mu, attenuation(metal_name, E), objs, (1e5, 1e5), 0.0, 10))
+    return cases
+
+
 # ----------------------------------------------------------------------------
 # Measurements
 # ----------------------------------------------------------------------------

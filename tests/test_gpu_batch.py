@@ -1,0 +1,85 @@
+"""Batched MAR-DEAM (deam_batch_*): scans of uneven size and view count iterated
+together must give what deam_iterate gives for each scan alone (same per-ray
+code; the backprojection tile shape the autotuner picks may differ from the
+single-scan one, which changes only the FP32 summation grouping)."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2202_00116_gb300 import build
+    build.build()
+    import paper_2202_00116_gb300 as p
+    return p
+
+
+def _rel(a, b):
+    a, b = a.double(), b.double()
+    return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+
+
+def _scans(pkg, n=4):
+    out = []
+    for case in synth.make_batch_cases(n, small=True):
+        d, metal = synth.measure(case, seed=2)
+        truth, _ = synth.voxelize(case)
+        mask = (metal >= case.metal_threshold).to(torch.uint8)
+        c0 = synth.initial_image(case, truth)
+        g = pkg.from_case(case)
+        g.set_data(d.cuda())
+        g.set_metal_mask(mask.cuda(), "ray")
+        out.append((g, c0))
+    return out
+
+
+@pytest.mark.parametrize("autotune", [True, False])   # tuned plan / the persistent plan
+def test_batch_matches_single_scans(pkg, autotune):
+    scans = _scans(pkg)
+    ref_imgs, ref_hist = [], []
+    for g, c0 in scans:
+        c = c0.clone().cuda()
+        ref_hist.append(g.iterate(c, 3))
+        ref_imgs.append(c)
+    batch = pkg.DeamBatch([g for g, _ in scans], autotune=autotune)
+    imgs = [c0.clone().cuda() for _, c0 in scans]
+    H = batch.iterate(imgs, 3)
+    assert H.shape == (len(scans), 3)
+    for i in range(len(scans)):
+        assert _rel(imgs[i], ref_imgs[i]) < 1e-6
+        np.testing.assert_allclose(H[i, 0], ref_hist[i][0], rtol=1e-12)
+        np.testing.assert_allclose(H[i], ref_hist[i], rtol=1e-7)
+        assert np.all(np.diff(H[i]) < 0)
+    info = batch.info()
+    if autotune:
+        assert min(info["tuning_ms"]["forward"]) > 0 and len(info["tuning_ms"]["backprojection"]) >= 2
+        assert {b["slab"] for b in info["backprojection"]} <= {2, 8, 16}
+        assert min(info["tuning_ms"]["plans"]) > 0 and info["plan"] in ("persistent", "per-scan graph branches")
+    # new image buffers: the graph is captured again and the iterations continue
+    imgs2 = [c.clone() for c in imgs]
+    H2 = batch.iterate(imgs2, 2)
+    for i, (g, _) in enumerate(scans):
+        c = ref_imgs[i].clone()
+        h = g.iterate(c, 2)
+        assert _rel(imgs2[i], c) < 2e-6
+        np.testing.assert_allclose(H2[i], h, rtol=1e-6)
+    batch.close()
+
+
+def test_batch_rejects_bad_input(pkg):
+    scans = _scans(pkg, 2)
+    g0 = scans[0][0]
+    with pytest.raises(pkg.DeamError):
+        pkg.DeamBatch([g0, g0])                 # a context twice
+    batch = pkg.DeamBatch([g for g, _ in scans], autotune=False)
+    with pytest.raises(ValueError):
+        batch.iterate([scans[0][1].cuda()], 1)  # one image for two scans
+    with pytest.raises(ValueError):
+        batch.iterate([c0 for _, c0 in scans], 1)  # host images are refused by the binding
+    batch.close()
