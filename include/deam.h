@@ -59,8 +59,10 @@ enum {
 enum { DEAM_GEOM_FAN2D = 0, DEAM_GEOM_HELICAL = 1 };
 
 enum {
-    DEAM_MASK_VOXEL_IMAGE = 0, /* m: float32 metal image M [nz][ny][nx]; mask = (A M >= t) */
-    DEAM_MASK_RAY = 1          /* m: uint8 [V][R][K], nonzero = metal-trace ray */
+    DEAM_MASK_VOXEL_IMAGE = 0,       /* m: float32 metal image M [nz][ny][nx]; mask = (A M >= t), both spectra */
+    DEAM_MASK_RAY = 1,               /* m: uint8 [V][R][K], nonzero = metal-trace ray for both spectra */
+    DEAM_MASK_RAY_PER_SPECTRUM = 2   /* m: uint8 [V][R][K], bit 0: on the trace T_L of the low-kVp data,
+                                        bit 1: on the trace T_H of the high-kVp data (Sec. 2.1) */
 };
 
 /* Scanner and volume geometry (lengths in mm, angles in rad). */
@@ -120,11 +122,16 @@ int deam_set_data(deam_ctx *ctx, const float *d, void *stream);
 /* Set the metal trace (Sec. 2.1: rays with T(y) >= t are "metal").  kind =
  * DEAM_MASK_VOXEL_IMAGE: m is the metal image M (host or device float32
  * [nz][ny][nx]), forward-projected on the GPU and thresholded at opts.metal_threshold
- * (T = t counts as metal).  kind = DEAM_MASK_RAY: m is a uint8 ray mask (host or
- * device), copied.  Until called, no ray is metal (plain DEAM). */
+ * (T = t counts as metal) for both spectra.  kind = DEAM_MASK_RAY: m is a uint8
+ * ray mask (host or device), nonzero = metal for both spectra.  kind =
+ * DEAM_MASK_RAY_PER_SPECTRUM: separate traces T_L, T_H as bits 0 and 1 (for
+ * scans whose two spectra see different system operators, e.g. motion between
+ * the acquisitions); the substitution p = q then applies per spectrum.  Until
+ * called, no ray is metal (plain DEAM). */
 int deam_set_metal_mask(deam_ctx *ctx, const void *m, int kind, void *stream);
 
-/* Copy the current metal mask (uint8 [V][R][K]) to device memory `mask`. */
+/* Copy the current metal mask (uint8 [V][R][K], bit j = on the trace of
+ * spectrum j) to device memory `mask`. */
 int deam_get_metal_mask(deam_ctx *ctx, uint8_t *mask, void *stream);
 
 /* Forward model at image c (device float32 [nz][ny][nx][2]): line integrals
@@ -166,6 +173,16 @@ int deam_objective(deam_ctx *ctx, const float *c, double *out, void *stream);
  * (nothing per energy bin is stored); *F (host, may be NULL) receives F(c).
  * Needs deam_set_data.  Deterministic. */
 int deam_gradient(deam_ctx *ctx, const float *c, float *grad, double *F, void *stream);
+
+/* Linear images of the basis components (Sec. 3): out[e] = a_e c_1 + b_e c_2 for
+ * n coefficient pairs coef[2e] = a_e, coef[2e+1] = b_e (host, 1 <= n <= 256).
+ * With (a_e, b_e) = (mu_1(E_e), mu_2(E_e)) these are virtual monoenergetic
+ * images mu(x, E) (paper Fig. 5: 20, 60, 140 keV); with (a, b) = sum_E w_j(E)
+ * (mu_1(E), mu_2(E)), w_j the normalised spectrum j, they are the
+ * spectrum-weighted averages of the VMIs shown as 90 and 140 kVp images.
+ * c: device float32 [nz][ny][nx][2]; out: device float32 [n][nz][ny][nx].
+ * Synchronises `stream`. */
+int deam_basis_images(deam_ctx *ctx, const float *c, const double *coef, int n, float *out, void *stream);
 
 /* Normaliser Z in use, and the number of (voxel, component) pairs left unchanged
  * by the last c-step (b~ <= 0 or b^ <= 0). Either pointer may be NULL. */

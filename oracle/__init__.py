@@ -180,10 +180,18 @@ class Oracle:
 
     def _dm(self, d, mask):
         d = _f64(_np(d)).reshape((2,) + self.ray_shape)
+        return d, self.mask_bits(mask)
+
+    def mask_bits(self, mask):
+        """Metal mask in the oracle's encoding (bit j: on the trace of spectrum j)
+        from None (no metal), a [V,R,K] mask (nonzero: both spectra) or a
+        per-spectrum [2,V,R,K] mask."""
         if mask is None:
-            mask = np.zeros(self.ray_shape, dtype=np.uint8)
-        mask = np.ascontiguousarray(_np(mask), dtype=np.uint8).reshape(self.ray_shape)
-        return d, mask
+            return np.zeros(self.ray_shape, dtype=np.uint8)
+        m = _np(mask)
+        if m.shape == (2,) + self.ray_shape:
+            return np.ascontiguousarray((m[0] != 0) * 1 + (m[1] != 0) * 2, dtype=np.uint8)
+        return np.ascontiguousarray((m.reshape(self.ray_shape) != 0) * 3, dtype=np.uint8)
 
     def ray_model(self, c, d, mask, rays):
         """Per-ray l [n,2], g [n,2], payload [n,4] = (B~1, B~2, B^1, B^2), f [n]."""
@@ -237,6 +245,14 @@ class Oracle:
         out = np.zeros(self.img_shape)
         self.L.or_gradient(C.byref(self.g), C.byref(self.m), _p(c), _p(d), _p(mask, C.c_uint8), _p(out))
         return out
+
+
+def basis_images(c, coef):
+    """out[e] = coef[e, 0] c_1 + coef[e, 1] c_2 (the VMI mu(x, E) = mu_1(E) c_1(x) +
+    mu_2(E) c_2(x) of Sec. 3 when coef = (mu_1(E), mu_2(E))), float64."""
+    c = _f64(_np(c))
+    coef = np.asarray(coef, dtype=np.float64).reshape(-1, 2)
+    return np.stack([a * c[..., 0] + b * c[..., 1] for a, b in coef])
 
 
 def from_case(case) -> Oracle:

@@ -27,6 +27,9 @@
  *
  * Layouts: image [nz][ny][nx][2] (c_1, c_2 interleaved), rays [V][R][K] with the
  * per-ray pair last, measurements d [2][V][R][K] (j = L, H), spectra [2][nE].
+ * Metal masks are uint8 [V][R][K] with bit j set when ray y lies on the metal
+ * trace T_j of spectrum j (Sec. 2.1: the traces differ when the two spectra's
+ * system operators differ; with one operator both bits are set together).
  * All arithmetic is double precision.  OpenMP runs independent rays in parallel;
  * backprojection scatters with atomic adds.
  */
@@ -319,7 +322,7 @@ void or_ray_model(const or_geometry *g, const or_model *m, const double *c, cons
                 spectral_sums(m, j, k, l1, l2, &gg, &s1, &s2);
                 double dt = d[j * nrays + y] > 0.0 ? d[j * nrays + y] : 0.0;
                 double rj = 1.0;   /* where g = 0 every q is 0 and r*S = 0 for any r */
-                if (!mask[y]) {
+                if (!(mask[y] & (1u << j))) {   /* bit j: ray on the metal trace T_j of spectrum j */
                     if (gg > 0.0) rj = dt / gg;
                     ff += idiv_term(dt, gg);
                 }
@@ -372,7 +375,7 @@ static double ray_pass(const or_geometry *g, const or_model *m, const double *c,
                 spectral_sums(m, j, k, l1, l2, &gg, &s1, &s2);
                 double dt = d[j * nrays + y] > 0.0 ? d[j * nrays + y] : 0.0;
                 double rj = 1.0;   /* where g = 0 every q is 0 and r*S = 0 for any r */
-                if (!mask[y]) {
+                if (!(mask[y] & (1u << j))) {   /* bit j: ray on the metal trace T_j of spectrum j */
                     if (gg > 0.0) rj = dt / gg;
                     F += idiv_term(dt, gg);
                 }
@@ -441,7 +444,8 @@ double or_normaliser(const or_geometry *g, const or_model *m) {
     return mumax * hmax;
 }
 
-/* Metal trace T(y) = sum_x h(x,y) M(x) (Sec. 2.1) and mask = (T >= t). */
+/* Metal trace T(y) = sum_x h(x,y) M(x) (Sec. 2.1) and mask = (T >= t) for both
+ * spectra (bits 0 and 1: one system operator). */
 void or_metal_trace(const or_geometry *g, const double *M, double t, double *T_out, uint8_t *mask) {
     const int RK = g->n_rows * g->n_channels;
     const long n = (long)g->n_views * RK;
@@ -456,7 +460,7 @@ void or_metal_trace(const or_geometry *g, const double *M, double t, double *T_o
             double s = 0.0;
             for (int i = 0; i < nt; i++) s += T[i].w * M[T[i].idx];
             T_out[q] = s;
-            mask[q] = (uint8_t)(s >= t);
+            mask[q] = (uint8_t)(s >= t ? 3 : 0);
         }
         free(T);
     }

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libdeam.so")
 
 DEAM_OK, DEAM_ERR_ARG, DEAM_ERR_CUDA, DEAM_ERR_OOM, DEAM_ERR_STATE, DEAM_ERR_TIMEOUT, DEAM_ERR_NUMERIC = range(7)
 FAN2D, HELICAL = 0, 1
-MASK_VOXEL_IMAGE, MASK_RAY = 0, 1
+MASK_VOXEL_IMAGE, MASK_RAY, MASK_RAY_PER_SPECTRUM = 0, 1, 2
 
 
 class deam_geometry(C.Structure):
@@ -60,7 +60,7 @@ class DeamError(RuntimeError):
 _lib = None
 EXPORTS = ["deam_init", "deam_set_data", "deam_set_metal_mask", "deam_get_metal_mask", "deam_forward",
            "deam_backproject", "deam_ray_terms", "deam_iterate", "deam_objective", "deam_info",
-           "deam_gradient", "deam_count_samples", "deam_profile", "deam_kernel_times", "deam_batch_create",
+           "deam_gradient", "deam_basis_images", "deam_count_samples", "deam_profile", "deam_kernel_times", "deam_batch_create",
            "deam_batch_iterate", "deam_batch_info", "deam_batch_destroy", "deam_objective_noalloc",
            "deam_destroy", "deam_last_error"]
 
@@ -86,6 +86,7 @@ def lib():
             "deam_objective": [vp, vp, pd, vp],
             "deam_info": [vp, pd, C.POINTER(C.c_longlong)],
             "deam_gradient": [vp, vp, vp, pd, vp],
+            "deam_basis_images": [vp, vp, pd, i, vp, vp],
             "deam_count_samples": [vp, C.POINTER(C.c_longlong), vp],
             "deam_profile": [vp, i],
             "deam_kernel_times": [vp, pd, C.POINTER(C.c_longlong), i],
@@ -186,9 +187,17 @@ class Deam:
             self.torch.cuda.current_stream(self.device).synchronize()
 
     def set_metal_mask(self, m, kind="ray"):
-        """kind='ray': uint8 [V, R, K]; kind='voxel': float32 metal image [nz, ny, nx]."""
+        """kind='ray': uint8 [V, R, K] (nonzero: both spectra); kind='per_spectrum':
+        bool/uint8 [2, V, R, K] traces (T_L, T_H), packed into bits 0 and 1;
+        kind='voxel': float32 metal image [nz, ny, nx]."""
         torch = self.torch
-        if kind == "ray":
+        if kind == "per_spectrum":
+            if tuple(m.shape) != (2,) + self.ray_shape:
+                raise ValueError(f"expected a mask of shape {(2,) + self.ray_shape}")
+            m = ((m[0] != 0).to(torch.uint8) + 2 * (m[1] != 0).to(torch.uint8)).contiguous()
+            p = self._arg(m, self.ray_shape, torch.uint8, True)
+            k = MASK_RAY_PER_SPECTRUM
+        elif kind == "ray":
             p = self._arg(m, self.ray_shape, torch.uint8, True)
             k = MASK_RAY
         else:
@@ -255,6 +264,32 @@ class Deam:
         _check(lib().deam_gradient(self._h, self._arg(c, self.img_shape, torch.float32),
                                    self._arg(out, self.img_shape, torch.float32), C.byref(F), self._stream()))
         return out, F.value
+
+    def basis_images(self, c, coef):
+        """out[e] = coef[e, 0] c_1 + coef[e, 1] c_2, float32 [n, nz, ny, nx]."""
+        torch = self.torch
+        coef = np.ascontiguousarray(np.asarray(coef, dtype=np.float64).reshape(-1, 2))
+        out = torch.empty((coef.shape[0],) + self.img_shape[:3], dtype=torch.float32, device=self.device)
+        _check(lib().deam_basis_images(self._h, self._arg(c, self.img_shape, torch.float32),
+                                       coef.ctypes.data_as(C.POINTER(C.c_double)), coef.shape[0],
+                                       C.c_void_p(out.data_ptr()), self._stream()))
+        return out
+
+    def vmi(self, c, energies_keV):
+        """Virtual monoenergetic images mu(x, E) = mu_1(E) c_1 + mu_2(E) c_2 (1/mm) at the
+        given energies; mu_i(E) interpolated linearly in log mu over the bin centres."""
+        if self._E is None:
+            raise ValueError("the context was created without bin energies")
+        E = np.asarray(energies_keV, dtype=np.float64).reshape(-1)
+        coef = np.stack([np.exp(np.interp(E, self._E, np.log(np.maximum(self._mu[i], 1e-300)))) for i in range(2)], 1)
+        return self.basis_images(c, coef)
+
+    def kvp_images(self, c):
+        """The two spectrum-weighted averages of the VMIs (low, high kVp):
+        sum_E w_j(E) mu(x, E) with w_j = I0_j / sum_E I0_j."""
+        w = self._I0 / self._I0.sum(axis=1, keepdims=True)
+        coef = np.stack([w @ self._mu[0], w @ self._mu[1]], 1)
+        return self.basis_images(c, coef)
 
     def info(self):
         Z = C.c_double()

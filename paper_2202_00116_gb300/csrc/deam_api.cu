@@ -82,7 +82,8 @@ static cudaError_t dalloc(T** p, size_t n) {
 
 static void free_ctx(deam_ctx* c) {
     void* ptrs[] = {c->view4, c->view_z, c->ip4, c->ipL, c->chan, c->row, c->bowtie, c->dt, c->mask, c->payload,
-                    c->volX, c->volY, c->partial, c->scal, c->hist, c->slab_views, c->skipped, c->c_stage};
+                    c->volX, c->volY, c->partial, c->scal, c->hist, c->slab_views, c->skipped, c->c_stage,
+                    c->coef};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete c;
@@ -393,9 +394,11 @@ int deam_set_metal_mask(deam_ctx* ctx, const void* m, int kind, void* stream) {
     DeviceGuard dg(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     const bool dev = is_device_ptr(m);
-    if (kind == DEAM_MASK_RAY) {
+    if (kind == DEAM_MASK_RAY || kind == DEAM_MASK_RAY_PER_SPECTRUM) {
         CK(cudaMemcpyAsync(ctx->mask, m, (size_t)ctx->nrays, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                            s));
+        CK(deam::launch_mask_bits(ctx->mask, ctx->nrays, kind == DEAM_MASK_RAY_PER_SPECTRUM, s));
+        if (!dev) CK(cudaStreamSynchronize(s));  // the caller's host buffer is released on return
     } else if (kind == DEAM_MASK_VOXEL_IMAGE) {
         const float* M = (const float*)m;
         if (!dev) {
@@ -582,6 +585,22 @@ int deam_gradient(deam_ctx* ctx, const float* c, float* grad, double* F, void* s
         CK(cudaStreamSynchronize(s));
         if (!isfinite(*F)) return fail(DEAM_ERR_NUMERIC, "objective is not finite");
     }
+    return DEAM_OK;
+}
+
+int deam_basis_images(deam_ctx* ctx, const float* c, const double* coef, int n, float* out, void* stream) {
+    CHECK_CTX(ctx);
+    if (!c || !coef || !out || n < 1 || n > 256) return fail(DEAM_ERR_ARG, "need c, out and 1..256 coefficient pairs");
+    for (int e = 0; e < 2 * n; ++e)
+        if (!isfinite(coef[e])) return fail(DEAM_ERR_ARG, "coefficients must be finite");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!ctx->coef) CK(dalloc(&ctx->coef, 256));
+    std::vector<float2> ab(n);
+    for (int e = 0; e < n; ++e) ab[e] = make_float2((float)coef[2 * e], (float)coef[2 * e + 1]);
+    CK(cudaMemcpyAsync(ctx->coef, ab.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, s));
+    CK(deam::launch_combine((const float2*)c, ctx->nvox, ctx->coef, n, out, s));
+    CK(cudaStreamSynchronize(s));  // the host coefficient buffer is released on return
     return DEAM_OK;
 }
 

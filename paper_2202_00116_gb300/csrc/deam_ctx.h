@@ -38,6 +38,7 @@ struct deam_ctx {
     int2* slab_views = nullptr;
     unsigned long long* skipped = nullptr;
     float2* c_stage = nullptr;
+    float2* coef = nullptr;  // deam_basis_images coefficients
     // per-kernel timing of deam_iterate (deam_profile)
     bool prof = false;
     double prof_ms[4] = {0, 0, 0, 0};

@@ -111,7 +111,7 @@ struct FwdArgs {
     float2* l_out;        // FWD_LINE(_G): [V][R][K] line integrals (nullable in LINE_G)
     float* g_out;         // FWD_LINE_G: [2][V][R][K] expected counts
     const float* dt;      // FWD_DEAM: d~ [2][V][R][K]
-    const uint8_t* mask;  // FWD_DEAM: [V][R][K] metal trace (nullable: none)
+    const uint8_t* mask;  // FWD_DEAM: [V][R][K] metal traces, bit j = spectrum j (nullable: none)
     const float* bowtie;  // [K] (nullable: 1)
     float4* payload;      // FWD_DEAM: [V][R][K] (B~1, B~2, D1, D2)
     double* partial;      // FWD_DEAM: per-block objective; FWD_MAX: per-block max; FWD_COUNT: samples
@@ -172,6 +172,8 @@ cudaError_t launch_forward(int mode, const Geo& G, const Spec& S, const FwdArgs&
 cudaError_t launch_backward(int mode, int slab, const Geo& G, const BwdArgs& A, cudaStream_t s);
 cudaError_t launch_sum_partials(const double* partial, int n, double* out, int do_max, cudaStream_t s);
 cudaError_t launch_clamp_copy(const float* d, float* dt, long long n, cudaStream_t s);
+cudaError_t launch_mask_bits(uint8_t* m, long long n, int per_spectrum, cudaStream_t s);
+cudaError_t launch_combine(const float2* c, long long nvox, const float2* ab, int n, float* out, cudaStream_t s);
 
 // Record an error message for deam_last_error() and return code (deam_api.cu).
 int set_error(int code, const char* msg);

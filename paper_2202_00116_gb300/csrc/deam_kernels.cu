@@ -104,7 +104,7 @@ __device__ __forceinline__ double fwd_ray(const Geo& G, const Spec& S, const Fwd
     if (MODE == FWD_LINE) {
         A.l_out[y] = make_float2(l1, l2);
     } else if (MODE == FWD_MASK) {
-        A.mask_out[y] = (uint8_t)(l1 >= A.threshold);
+        A.mask_out[y] = (uint8_t)(l1 >= A.threshold ? 3 : 0);  // one operator: both spectra
     } else if (MODE == FWD_MAX) {
         out = (double)l1;
     } else if (MODE == FWD_COUNT) {
@@ -122,10 +122,12 @@ __device__ __forceinline__ double fwd_ray(const Geo& G, const Spec& S, const Fwd
         const float bk = A.bowtie ? __ldg(&A.bowtie[k]) : 1.f;
         gl *= bk; gh *= bk; s1l *= bk; s2l *= bk; s1h *= bk; s2h *= bk;
         float4 P = make_float4(s1l + s1h, s2l + s2h, 0.f, 0.f);
-        const bool metal = A.mask != nullptr && A.mask[y] != 0;
-        if (!metal) {
-            float f = 0.f;
-            const float dl = __ldcs(&A.dt[y]), dh = __ldcs(&A.dt[nrays + y]);
+        // bit j of the mask: the ray is on the metal trace of spectrum j, where
+        // p = q (r_j = 1): no data term and no ratio contribution (Eq. 11)
+        const unsigned mk = A.mask != nullptr ? A.mask[y] : 0u;
+        float f = 0.f;
+        if (!(mk & 1u)) {
+            const float dl = __ldcs(&A.dt[y]);
             if (gl > 0.f) {
                 const float u = (dl - gl) / gl;  // r_L - 1
                 P.z = fmaf(u, s1l, P.z);
@@ -134,6 +136,9 @@ __device__ __forceinline__ double fwd_ray(const Geo& G, const Spec& S, const Fwd
             } else if (dl > 0.f) {
                 f = INFINITY;
             }
+        }
+        if (!(mk & 2u)) {
+            const float dh = __ldcs(&A.dt[nrays + y]);
             if (gh > 0.f) {
                 const float u = (dh - gh) / gh;  // r_H - 1
                 P.z = fmaf(u, s1h, P.z);
@@ -142,8 +147,8 @@ __device__ __forceinline__ double fwd_ray(const Geo& G, const Spec& S, const Fwd
             } else if (dh > 0.f) {
                 f = INFINITY;
             }
-            out = (double)f;
         }
+        out = (double)f;
         __stcs(&A.payload[y], P);
     }
     return out;
@@ -550,6 +555,29 @@ __global__ void __launch_bounds__(256) sum_partials_kernel(const double* __restr
     if (threadIdx.x == 0) *out = sh[0];
 }
 
+// out[e][x] = a_e c_1(x) + b_e c_2(x) for n coefficient pairs: virtual
+// monoenergetic images (a, b) = (mu_1(E), mu_2(E)) and spectrum-weighted
+// averages of them.  HBM-bound: reads c once per voxel, writes n floats.
+__global__ void combine_kernel(const float2* __restrict__ c, long long nvox, const float2* __restrict__ ab, int n,
+                               float* __restrict__ out) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nvox;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float2 v = c[i];
+        for (int e = 0; e < n; ++e) {
+            const float2 w = __ldg(&ab[e]);
+            out[(long long)e * nvox + i] = fmaf(w.x, v.x, w.y * v.y);
+        }
+    }
+}
+
+// Ray masks to the per-spectrum bit encoding: nonzero = both spectra, or the
+// caller's bits 0 (low kVp) and 1 (high kVp) kept as given.
+__global__ void mask_bits_kernel(uint8_t* __restrict__ m, long long n, int per_spectrum) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        m[i] = per_spectrum ? (uint8_t)(m[i] & 3u) : (uint8_t)(m[i] ? 3u : 0u);
+}
+
 // d~ = max(d, 0): the nonnegative substitution of the measurements (Sec. 2.1).
 __global__ void clamp_copy_kernel(const float* __restrict__ d, float* __restrict__ dt, long long n) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -684,6 +712,16 @@ cudaError_t launch_inplane_table(const Geo& G, float4* ip4, float* ipL, cudaStre
 
 cudaError_t launch_sum_partials(const double* partial, int n, double* out, int do_max, cudaStream_t s) {
     sum_partials_kernel<<<1, 256, 0, s>>>(partial, n, out, do_max);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_combine(const float2* c, long long nvox, const float2* ab, int n, float* out, cudaStream_t s) {
+    combine_kernel<<<grid_for(nvox, 256), 256, 0, s>>>(c, nvox, ab, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mask_bits(uint8_t* m, long long n, int per_spectrum, cudaStream_t s) {
+    mask_bits_kernel<<<grid_for(n, 256), 256, 0, s>>>(m, n, per_spectrum);
     return cudaGetLastError();
 }
 

@@ -294,3 +294,50 @@ def test_precision_report(pkg, name, record_property, capsys):
     assert max(errs[x] for x in ("line_integrals", "expected_counts", "B_tilde", "B_hat")) < 1e-5
     assert errs["objective"] < 1e-5 and errs["objective_history_max"] < 1e-5
     assert errs["image_after_10"] < 1e-4
+
+
+def test_per_spectrum_traces_match_oracle(pkg):
+    # separate traces T_L, T_H (Sec. 2.1): parity with the oracle, and the
+    # low-kVp data on T_L never matters (bitwise)
+    case, d, mask, M, c0 = case_data("t3d")
+    m = mask.bool()
+    gen = torch.Generator().manual_seed(3)
+    mH = m & (torch.rand(m.shape, generator=gen) < 0.5)
+    per = torch.stack([m, mH])
+    gpu = pkg.from_case(case)
+    gpu.set_data(d.cuda())
+    gpu.set_metal_mask(per.cuda(), "per_spectrum")
+    O = oracle_of(case)
+    bits = O.mask_bits(per.numpy())
+    assert np.array_equal(gpu.metal_mask().cpu().numpy(), bits) and set(np.unique(bits)) == {0, 1, 3}
+    c = c0.clone().cuda()
+    hist = gpu.iterate(c, 5)
+    c_ref, h_ref, _ = O.iterate(c0.double().numpy(), d.double().numpy(), per.numpy(), n_iter=5)
+    assert rel_l2(c.cpu().numpy(), c_ref) < 1e-4
+    np.testing.assert_allclose(hist, h_ref, rtol=1e-5)
+    d2 = d.clone()
+    d2[0][m] = 3.0e5
+    gpu.set_data(d2.cuda())
+    c2 = c0.clone().cuda()
+    h2 = gpu.iterate(c2, 5)
+    assert torch.equal(c2, c) and np.array_equal(h2, hist)
+
+
+def test_basis_images_match_oracle(pkg):
+    # VMI mu(x, E) = mu_1(E) c_1 + mu_2(E) c_2 and the spectrum-weighted images (Sec. 3)
+    import oracle
+    case, d, mask, M, c0 = case_data("c0")
+    gpu = pkg.from_case(case)
+    coef = np.array([[0.02, 0.05], [1.0, 0.0], [-0.3, 2.0]])
+    out = gpu.basis_images(c0.cuda(), coef)
+    assert rel_l2(out.cpu().numpy(), oracle.basis_images(c0.double().numpy(), coef)) < 1e-6
+    # a pure basis-1 image shows mu_1(E) everywhere at a bin centre
+    ones = torch.zeros_like(c0)
+    ones[..., 0] = 1.0
+    e = 40
+    vmi = gpu.vmi(ones.cuda(), [case.energies[e]]).cpu().numpy()
+    np.testing.assert_allclose(vmi, case.mu[0, e], rtol=1e-6)
+    kvp = gpu.kvp_images(c0.cuda()).cpu().numpy()
+    w = case.I0 / case.I0.sum(1, keepdims=True)
+    ref = oracle.basis_images(c0.double().numpy(), np.stack([w @ case.mu[0], w @ case.mu[1]], 1))
+    assert kvp.shape == (2,) + tuple(c0.shape[:3]) and rel_l2(kvp, ref) < 1e-6

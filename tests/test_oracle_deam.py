@@ -186,9 +186,10 @@ def test_metal_trace_threshold(oracle_lib):
     hit = metal > 1.0
     assert np.abs(T[hit] - metal[hit]).mean() < 0.1 * metal[hit].mean()
     assert np.array_equal(mask.astype(bool), T >= case.metal_threshold)
+    assert set(np.unique(mask)) <= {0, 3}        # one system operator: both spectra's bits
     t_exact = float(T[hit][0])
     _, m2 = O.metal_trace(M, t_exact)
-    assert m2.reshape(-1)[np.flatnonzero(hit.reshape(-1))[0]] == 1
+    assert m2.reshape(-1)[np.flatnonzero(hit.reshape(-1))[0]] == 3
     _, m3 = O.metal_trace(M, np.inf)
     assert m3.sum() == 0
 
@@ -225,3 +226,32 @@ def test_backprojected_sums_are_adjoint_of_payload(oracle_lib):
     np.testing.assert_allclose(bt, O.adjoint(pay[..., :2]), rtol=1e-11, atol=1e-9)
     np.testing.assert_allclose(bh, O.adjoint(pay[..., 2:]), rtol=1e-11, atol=1e-9)
     assert F == pytest.approx(f.sum(), rel=1e-12)
+
+
+def test_per_spectrum_traces(oracle_lib):
+    # Sec. 2.1: with different traces T_L, T_H the substitution p = q applies per
+    # spectrum.  Data of spectrum j on its own trace is never used; data of the
+    # other spectrum on those rays is.  Equal traces reproduce the joint mask.
+    import oracle
+    case, d, mask, c0, _, _ = _noisy_case("t3d")
+    O = oracle.from_case(case)
+    m = mask.astype(bool)
+    rng = np.random.default_rng(11)
+    mL = m.copy()
+    mH = m & (rng.random(m.shape) < 0.5)          # a smaller high-kVp trace
+    per = np.stack([mL, mH])
+    ca, ha, _ = O.iterate(c0, d, per, n_iter=2)
+    cj, hj, _ = O.iterate(c0, d, np.stack([m, m]), n_iter=2)
+    cb, hb, _ = O.iterate(c0, d, mask, n_iter=2)
+    np.testing.assert_allclose(cj, cb, rtol=0, atol=1e-13)
+    d2 = d.copy()
+    d2[0][mL] = rng.uniform(0, 1e6, size=mL.sum())  # low-kVp data on T_L: ignored
+    c2, h2, _ = O.iterate(c0, d2, per, n_iter=2)
+    np.testing.assert_allclose(c2, ca, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(h2, ha, rtol=1e-14)
+    d3 = d.copy()
+    only_L = mL & ~mH
+    d3[1][only_L] *= 1.3                             # high-kVp data there is used
+    c3, _, _ = O.iterate(c0, d3, per, n_iter=1)
+    assert np.abs(c3 - O.iterate(c0, d, per, n_iter=1)[0]).max() > 1e-6
+    assert ha[0] > hb[0]                             # fewer excluded rays: more data misfit
