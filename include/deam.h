@@ -99,6 +99,8 @@ typedef struct deam_basis {
 typedef struct deam_options {
     double metal_threshold; /* t of Sec. 2.1 in mm of metal path; <= 0: half the smallest voxel edge */
     double Z;               /* c-step normaliser; <= 0: max_E(mu_1+mu_2) * max_y sum_x h(x,y) */
+    double penalty_lambda;  /* lambda of Eq. (6); 0 (default): unregularised MAR-DEAM */
+    double penalty_delta;   /* delta of Eq. (7) (> 0 when lambda > 0) */
     int clamp_nonneg;       /* 1: clamp c_i >= 0 after each c-step (the paper is silent; default 0) */
     int reserved[7];        /* zero */
 } deam_options;
@@ -183,6 +185,16 @@ int deam_gradient(deam_ctx *ctx, const float *c, float *grad, double *F, void *s
  * c: device float32 [nz][ny][nx][2]; out: device float32 [n][nz][ny][nx].
  * Synchronises `stream`. */
 int deam_basis_images(deam_ctx *ctx, const float *c, const double *coef, int n, float *out, void *stream);
+
+/* The penalty R(c) of Eqs. (6)-(7) with the context's lambda and delta into *R
+ * (host): R = lambda sum_i sum_x sum_{x~ in N_x} w(x,x~) phi(c_i(x) - c_i(x~)),
+ * N_x the 26 neighbours inside the volume, w = 1/physical distance,
+ * phi(u) = delta^2 (|u|/delta - log(1 + |u|/delta)) (the convex reading of the
+ * garbled Eq. 7).  With lambda > 0, deam_iterate's c-step minimises the DEAM
+ * surrogate plus De Pierro's separable surrogate of R per voxel, so F + R does
+ * not increase; voxels no data reaches are then moved by the penalty alone.
+ * c: device float32 [nz][ny][nx][2]. */
+int deam_penalty(deam_ctx *ctx, const float *c, double *R, void *stream);
 
 /* Normaliser Z in use, and the number of (voxel, component) pairs left unchanged
  * by the last c-step (b~ <= 0 or b^ <= 0). Either pointer may be NULL. */

@@ -84,6 +84,9 @@ def lib():
             "or_metal_trace": (None, [G, pd, d, pd, pu8]),
             "or_iterate": (l, [G, M, pd, pd, pu8, i, pd, d, i, i, i]),
             "or_gradient": (None, [G, M, pd, pd, pu8, pd]),
+            "or_phi": (d, [d, d]),
+            "or_penalty": (d, [G, pd, d, d]),
+            "or_iterate_reg": (l, [G, M, pd, pd, pu8, i, pd, pd, d, i, d, d]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -239,12 +242,31 @@ class Oracle:
                                     n_iter, _p(hist), float(Z), int(clamp_nonneg), v0, v1)
         return c, hist[:n_iter], skipped
 
+    def penalty(self, c, lam, delta):
+        """R(c) of Eqs. (6)-(7) (26 neighbours, w = 1/distance, convex phi reading)."""
+        c = _f64(_np(c)).reshape(self.img_shape)
+        return self.L.or_penalty(C.byref(self.g), _p(c), float(lam), float(delta))
+
+    def iterate_reg(self, c, d, mask=None, n_iter=1, lam=0.0, delta=1.0, Z=0.0, clamp_nonneg=False):
+        """Regularised MAR-DEAM: returns (c_new, hist_F, hist_R, skipped)."""
+        c = _f64(_np(c)).reshape(self.img_shape).copy()
+        d, mask = self._dm(d, mask)
+        hF, hR = np.zeros(max(n_iter, 1)), np.zeros(max(n_iter, 1))
+        sk = self.L.or_iterate_reg(C.byref(self.g), C.byref(self.m), _p(c), _p(d), _p(mask, C.c_uint8), n_iter,
+                                   _p(hF), _p(hR), float(Z), int(clamp_nonneg), float(lam), float(delta))
+        return c, hF[:n_iter], hR[:n_iter], sk
+
     def gradient(self, c, d, mask=None):
         c = _f64(_np(c)).reshape(self.img_shape)
         d, mask = self._dm(d, mask)
         out = np.zeros(self.img_shape)
         self.L.or_gradient(C.byref(self.g), C.byref(self.m), _p(c), _p(d), _p(mask, C.c_uint8), _p(out))
         return out
+
+
+def phi(u, delta):
+    """phi(u) = delta^2 (|u|/delta - log(1 + |u|/delta)) (the convex reading of Eq. 7)."""
+    return lib().or_phi(float(u), float(delta))
 
 
 def basis_images(c, coef):

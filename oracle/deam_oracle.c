@@ -24,6 +24,7 @@
  *     cites this update from O'Sullivan & Benac instead of printing it; it follows
  *     from Eqs. (5), (8)-(11) by the alternating-minimisation surrogate argument.
  *     Voxels with b~_i <= 0 or b^_i <= 0 are left unchanged.
+ *   - regularised c-step (Eqs. 6-7): see or_iterate_reg below.
  *
  * Layouts: image [nz][ny][nx][2] (c_1, c_2 interleaved), rays [V][R][K] with the
  * per-ray pair last, measurements d [2][V][R][K] (j = L, H), spectra [2][nE].
@@ -466,6 +467,154 @@ void or_metal_trace(const or_geometry *g, const double *M, double t, double *T_o
     }
 }
 
+/* ---- Penalty of Eqs. (6)-(7) ------------------------------------------------
+ * R(c) = lambda sum_i sum_x sum_{x~ in N_x} w(x,x~) phi(c_i(x) - c_i(x~)),
+ * N_x = the 26 neighbours of x inside the volume, w = 1 / physical distance,
+ * phi(u) = delta^2 (|u|/delta - log(1 + |u|/delta)) (the printed phi has
+ * "log(1 - |t/delta|)", undefined for |t| >= delta and not convex; this is the
+ * convex reading), so phi'(u) = u / (1 + |u|/delta), phi''(u) = 1/(1 + |u|/delta)^2. */
+double or_phi(double u, double delta) {
+    double a = fabs(u) / delta;
+    return delta * delta * (a - log1p(a));
+}
+
+static double phi_d1(double u, double delta) { return u / (1.0 + fabs(u) / delta); }
+
+static double phi_d2(double u, double delta) {
+    double a = 1.0 + fabs(u) / delta;
+    return 1.0 / (a * a);
+}
+
+static double nb_weight(const or_geometry *g, int ox, int oy, int oz) {
+    double x = ox * g->dx, y = oy * g->dy, z = oz * g->dz;
+    return 1.0 / sqrt(x * x + y * y + z * z);
+}
+
+/* R(c) over the whole volume (each ordered pair (x, x~) counted, as printed). */
+double or_penalty(const or_geometry *g, const double *c, double lambda, double delta) {
+    double R = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : R) collapse(2)
+    for (int iz = 0; iz < g->nz; iz++)
+        for (int iy = 0; iy < g->ny; iy++)
+            for (int ix = 0; ix < g->nx; ix++) {
+                long x = ((long)iz * g->ny + iy) * g->nx + ix;
+                for (int oz = -1; oz <= 1; oz++)
+                    for (int oy = -1; oy <= 1; oy++)
+                        for (int ox = -1; ox <= 1; ox++) {
+                            if (!ox && !oy && !oz) continue;
+                            int jx = ix + ox, jy = iy + oy, jz = iz + oz;
+                            if (jx < 0 || jy < 0 || jz < 0 || jx >= g->nx || jy >= g->ny || jz >= g->nz) continue;
+                            long xn = ((long)jz * g->ny + jy) * g->nx + jx;
+                            double w = nb_weight(g, ox, oy, oz);
+                            for (int i = 0; i < 2; i++) R += w * or_phi(c[2 * x + i] - c[2 * xn + i], delta);
+                        }
+            }
+    return lambda * R;
+}
+
+/* Regularised c-step (De Pierro's separable surrogate of the convex pairwise
+ * penalty added to the DEAM surrogate).  Summing the two halves of every pair
+ * that involves x, voxel x and component i minimise, over t = c_i(x),
+ *   G(t) = bh (t - ck) + (bt / Z) exp(-Z (t - ck)) + lambda sum_x~ w phi(2 t - ck - ck_x~)
+ * whose derivative is increasing.  Root of G' by bisection-safeguarded Newton
+ * in a bracket that holds because |phi'| < delta. */
+static double reg_solve(double ck, double bt, double bh, double Z, double lambda, double delta, const double *m,
+                        const double *w, int nn) {
+    /* m[n] = ck + ck_x~; G'(t) = bh - bt e^{-Z(t-ck)} + 2 lambda sum w phi'(2t - m) */
+    double pmax = 0.0, lo, hi;
+    for (int n = 0; n < nn; n++) pmax += 2.0 * lambda * w[n] * delta;
+    if (bt > 0.0) {
+        double a = bh + pmax, b = bh - pmax;
+        lo = ck - log(a / bt) / Z;
+        hi = b > 0.0 ? ck - log(b / bt) / Z : 1e300;
+        if (!(hi < 1e300)) {
+            /* G' < 0 only below some finite t: widen until G'(hi) > 0 */
+            hi = lo + 1.0;
+            for (int it = 0; it < 200; it++) {
+                double gp = bh - bt * exp(-Z * (hi - ck));
+                for (int n = 0; n < nn; n++) gp += 2.0 * lambda * w[n] * phi_d1(2.0 * hi - m[n], delta);
+                if (gp > 0.0) break;
+                hi = lo + 2.0 * (hi - lo);
+            }
+        }
+    } else {
+        lo = 1e300;
+        hi = -1e300;
+        for (int n = 0; n < nn; n++) {
+            lo = fmin(lo, 0.5 * m[n]);
+            hi = fmax(hi, 0.5 * m[n]);
+        }
+    }
+    double t = 0.5 * (lo + hi);
+    for (int it = 0; it < 200; it++) {
+        double gp = bh, gpp = 0.0;
+        if (bt > 0.0) {
+            double e = bt * exp(-Z * (t - ck));
+            gp -= e;
+            gpp += Z * e;
+        }
+        for (int n = 0; n < nn; n++) {
+            double u = 2.0 * t - m[n];
+            gp += 2.0 * lambda * w[n] * phi_d1(u, delta);
+            gpp += 4.0 * lambda * w[n] * phi_d2(u, delta);
+        }
+        if (gp > 0.0) hi = t;
+        else lo = t;
+        double tn = gpp > 0.0 ? t - gp / gpp : 0.5 * (lo + hi);
+        if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+        if (fabs(tn - t) <= 1e-15 * (1.0 + fabs(t)) || hi - lo <= 1e-15 * (1.0 + fabs(t))) {
+            t = tn;
+            break;
+        }
+        t = tn;
+    }
+    return t;
+}
+
+static long c_step_reg(const or_geometry *g, double *c, const double *bt, const double *bh, double Z, double lambda,
+                       double delta, int clamp_nonneg) {
+    const long nvox = (long)g->nx * g->ny * g->nz;
+    double *ck = (double *)malloc(sizeof(double) * 2 * nvox);
+    memcpy(ck, c, sizeof(double) * 2 * nvox);
+    long skipped = 0;
+#pragma omp parallel for schedule(static) reduction(+ : skipped) collapse(2)
+    for (int iz = 0; iz < g->nz; iz++)
+        for (int iy = 0; iy < g->ny; iy++)
+            for (int ix = 0; ix < g->nx; ix++) {
+                long x = ((long)iz * g->ny + iy) * g->nx + ix;
+                for (int i = 0; i < 2; i++) {
+                    double m[26], w[26];
+                    int nn = 0;
+                    for (int oz = -1; oz <= 1; oz++)
+                        for (int oy = -1; oy <= 1; oy++)
+                            for (int ox = -1; ox <= 1; ox++) {
+                                if (!ox && !oy && !oz) continue;
+                                int jx = ix + ox, jy = iy + oy, jz = iz + oz;
+                                if (jx < 0 || jy < 0 || jz < 0 || jx >= g->nx || jy >= g->ny || jz >= g->nz) continue;
+                                long xn = ((long)jz * g->ny + jy) * g->nx + jx;
+                                m[nn] = ck[2 * x + i] + ck[2 * xn + i];
+                                w[nn] = nb_weight(g, ox, oy, oz);
+                                nn++;
+                            }
+                    double b_t = bt[2 * x + i], b_h = bh[2 * x + i];
+                    if (b_t > 0.0 && !(b_h > 0.0)) {  /* b^ <= 0: the data term is unbounded below */
+                        skipped++;
+                        continue;
+                    }
+                    if (!(b_t > 0.0) && nn == 0) {
+                        skipped++;
+                        continue;
+                    }
+                    double t = reg_solve(ck[2 * x + i], b_t > 0.0 ? b_t : 0.0, b_t > 0.0 ? b_h : 0.0, Z, lambda,
+                                         delta, m, w, nn);
+                    if (clamp_nonneg && t < 0.0) t = 0.0;
+                    c[2 * x + i] = t;
+                }
+            }
+    free(ck);
+    return skipped;
+}
+
 /* The c-step: c_i <- c_i - ln(b^_i / b~_i) / Z where both sums are positive.
  * Returns the number of (voxel, component) pairs left unchanged. */
 static long c_step(long nvox, double *c, const double *bt, const double *bh, double Z, int clamp_nonneg) {
@@ -485,6 +634,25 @@ static long c_step(long nvox, double *c, const double *bt, const double *bh, dou
 /* n_iter MAR-DEAM iterations in place on c.  hist[k] = F(c^k) before update k.
  * Z <= 0 selects the normaliser above.  Returns the skip count of the last c-step.
  * Views [v0, v1) restrict the rays used (the full method uses all views). */
+long or_iterate_reg(const or_geometry *g, const or_model *m, double *c, const double *d, const uint8_t *mask,
+                    int n_iter, double *hist, double *hist_R, double Z, int clamp_nonneg, double lambda,
+                    double delta) {
+    const long nvox = (long)g->nx * g->ny * g->nz;
+    if (Z <= 0.0) Z = or_normaliser(g, m);
+    double *bt = (double *)malloc(sizeof(double) * 2 * nvox);
+    double *bh = (double *)malloc(sizeof(double) * 2 * nvox);
+    long skipped = 0;
+    for (int it = 0; it < n_iter; it++) {
+        double F = ray_pass(g, m, c, d, mask, bt, bh, 0, g->n_views);
+        if (hist) hist[it] = F;
+        if (hist_R) hist_R[it] = or_penalty(g, c, lambda, delta);
+        skipped = c_step_reg(g, c, bt, bh, Z, lambda, delta, clamp_nonneg);
+    }
+    free(bt);
+    free(bh);
+    return skipped;
+}
+
 long or_iterate(const or_geometry *g, const or_model *m, double *c, const double *d, const uint8_t *mask,
                 int n_iter, double *hist, double Z, int clamp_nonneg, int v0, int v1) {
     const long nvox = (long)g->nx * g->ny * g->nz;

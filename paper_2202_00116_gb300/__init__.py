@@ -47,8 +47,8 @@ class deam_basis(C.Structure):
 
 
 class deam_options(C.Structure):
-    _fields_ = [("metal_threshold", C.c_double), ("Z", C.c_double), ("clamp_nonneg", C.c_int),
-                ("reserved", C.c_int * 7)]
+    _fields_ = [("metal_threshold", C.c_double), ("Z", C.c_double), ("penalty_lambda", C.c_double),
+                ("penalty_delta", C.c_double), ("clamp_nonneg", C.c_int), ("reserved", C.c_int * 7)]
 
 
 class DeamError(RuntimeError):
@@ -60,7 +60,7 @@ class DeamError(RuntimeError):
 _lib = None
 EXPORTS = ["deam_init", "deam_set_data", "deam_set_metal_mask", "deam_get_metal_mask", "deam_forward",
            "deam_backproject", "deam_ray_terms", "deam_iterate", "deam_objective", "deam_info",
-           "deam_gradient", "deam_basis_images", "deam_count_samples", "deam_profile", "deam_kernel_times", "deam_batch_create",
+           "deam_gradient", "deam_penalty", "deam_basis_images", "deam_count_samples", "deam_profile", "deam_kernel_times", "deam_batch_create",
            "deam_batch_iterate", "deam_batch_info", "deam_batch_destroy", "deam_objective_noalloc",
            "deam_destroy", "deam_last_error"]
 
@@ -87,6 +87,7 @@ def lib():
             "deam_info": [vp, pd, C.POINTER(C.c_longlong)],
             "deam_gradient": [vp, vp, vp, pd, vp],
             "deam_basis_images": [vp, vp, pd, i, vp, vp],
+            "deam_penalty": [vp, vp, pd, vp],
             "deam_count_samples": [vp, C.POINTER(C.c_longlong), vp],
             "deam_profile": [vp, i],
             "deam_kernel_times": [vp, pd, C.POINTER(C.c_longlong), i],
@@ -122,7 +123,7 @@ class Deam:
     """
 
     def __init__(self, geo, I0, mu, bowtie=None, energies=None, metal_threshold=0.0, Z=0.0,
-                 clamp_nonneg=False, device=None):
+                 clamp_nonneg=False, penalty_lambda=0.0, penalty_delta=1.0, device=None):
         import torch
         self.torch = torch
         if device is None:
@@ -142,7 +143,8 @@ class Deam:
         sp = deam_spectra(nE, self._E.ctypes.data_as(P) if self._E is not None else P(),
                           self._I0.ctypes.data_as(P), self._bow.ctypes.data_as(P) if self._bow is not None else P())
         ba = deam_basis(self._mu.shape[1], self._mu.ctypes.data_as(P))
-        op = deam_options(float(metal_threshold), float(Z), int(bool(clamp_nonneg)))
+        op = deam_options(float(metal_threshold), float(Z), float(penalty_lambda), float(penalty_delta),
+                          int(bool(clamp_nonneg)))
         h = C.c_void_p()
         self._h = None
         if torch.cuda.is_available():
@@ -264,6 +266,13 @@ class Deam:
         _check(lib().deam_gradient(self._h, self._arg(c, self.img_shape, torch.float32),
                                    self._arg(out, self.img_shape, torch.float32), C.byref(F), self._stream()))
         return out, F.value
+
+    def penalty(self, c):
+        """R(c) of Eqs. (6)-(7) with the context's lambda and delta."""
+        R = C.c_double()
+        _check(lib().deam_penalty(self._h, self._arg(c, self.img_shape, self.torch.float32), C.byref(R),
+                                  self._stream()))
+        return R.value
 
     def basis_images(self, c, coef):
         """out[e] = coef[e, 0] c_1 + coef[e, 1] c_2, float32 [n, nz, ny, nx]."""

@@ -83,7 +83,7 @@ static cudaError_t dalloc(T** p, size_t n) {
 static void free_ctx(deam_ctx* c) {
     void* ptrs[] = {c->view4, c->view_z, c->ip4, c->ipL, c->chan, c->row, c->bowtie, c->dt, c->mask, c->payload,
                     c->volX, c->volY, c->partial, c->scal, c->hist, c->slab_views, c->skipped, c->c_stage,
-                    c->coef};
+                    c->coef, c->sums};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete c;
@@ -179,6 +179,17 @@ deam::FwdArgs deam::fwd_args(deam_ctx* ctx) {
     return A;
 }
 
+void deam::set_penalty_args(const deam_ctx* ctx, BwdArgs& B) {
+    B.sums = ctx->lambda > 0.0 ? ctx->sums : nullptr;
+    B.lambda = (float)ctx->lambda;
+    B.delta = (float)ctx->delta;
+    B.Z = (float)ctx->Z;
+    B.pdx = (float)ctx->geo.dx;
+    B.pdy = (float)ctx->geo.dy;
+    B.pdz = (float)ctx->geo.dz;
+    B.volX = ctx->volX;
+}
+
 extern "C" {
 
 const char* deam_last_error(void) { return g_err.c_str(); }
@@ -191,7 +202,10 @@ int deam_init(const deam_geometry* geom, const deam_spectra* spectra, const deam
     if (!why.empty()) return fail(DEAM_ERR_ARG, why);
     deam_options o{};
     if (opts) o = *opts;
-    if (!isfinite(o.metal_threshold) || !isfinite(o.Z)) return fail(DEAM_ERR_ARG, "options must be finite");
+    if (!isfinite(o.metal_threshold) || !isfinite(o.Z) || !isfinite(o.penalty_lambda) || !isfinite(o.penalty_delta))
+        return fail(DEAM_ERR_ARG, "options must be finite");
+    if (o.penalty_lambda < 0.0 || (o.penalty_lambda > 0.0 && !(o.penalty_delta > 0.0)))
+        return fail(DEAM_ERR_ARG, "need penalty_lambda >= 0 and penalty_delta > 0 when penalty_lambda > 0");
 
     deam_ctx* ctx = new deam_ctx();
     const deam_geometry& g = *geom;
@@ -203,6 +217,8 @@ int deam_init(const deam_geometry* geom, const deam_spectra* spectra, const deam
     ctx->nrays = (long long)g.n_views * g.n_rows * g.n_channels;
     ctx->nvox = (long long)g.nx * g.ny * g.nz;
     ctx->clamp = o.clamp_nonneg ? 1 : 0;
+    ctx->lambda = o.penalty_lambda;
+    ctx->delta = o.penalty_lambda > 0.0 ? o.penalty_delta : 1.0;
     ctx->threshold = o.metal_threshold > 0.0 ? o.metal_threshold
                                              : 0.5 * std::min(g.dx, std::min(g.dy, g.nz > 1 ? g.dz : g.dx));
     ctx->slab = deam::pick_slab(g.nz, g.n_rows, g.dz, g.row_pitch, g.sid, g.sdd);
@@ -296,6 +312,7 @@ int deam_init(const deam_geometry* geom, const deam_spectra* spectra, const deam
     A(dalloc(&ctx->scal, 4));
     A(dalloc(&ctx->skipped, 1));
     if (spectra->bowtie) A(dalloc(&ctx->bowtie, g.n_channels));
+    if (ctx->lambda > 0.0) A(dalloc(&ctx->sums, (size_t)ctx->nvox));
     if (e != cudaSuccess) {
         cudaGetLastError();
         free_ctx(ctx);
@@ -518,6 +535,7 @@ int deam_iterate(deam_ctx* ctx, float* c, int n_iter, double* hist, void* stream
     B.invZ = (float)(1.0 / ctx->Z);
     B.clamp_nonneg = ctx->clamp;
     B.skipped = ctx->skipped;
+    deam::set_penalty_args(ctx, B);
     std::vector<cudaEvent_t> ev;
     if (ctx->prof) {
         ev.resize((size_t)5 * n_iter);
@@ -539,6 +557,7 @@ int deam_iterate(deam_ctx* ctx, float* c, int n_iter, double* hist, void* stream
         CK(cudaMemsetAsync(ctx->skipped, 0, sizeof(unsigned long long), s));
         if (e) CK(cudaEventRecord(e[3], s));
         CK(deam::launch_backward(deam::BWD_UPDATE, ctx->slab, ctx->G, B, s));
+        if (B.sums) CK(deam::launch_reg_update(ctx->G, B, s));
         if (e) CK(cudaEventRecord(e[4], s));
     }
     unsigned long long sk = 0;
@@ -585,6 +604,20 @@ int deam_gradient(deam_ctx* ctx, const float* c, float* grad, double* F, void* s
         CK(cudaStreamSynchronize(s));
         if (!isfinite(*F)) return fail(DEAM_ERR_NUMERIC, "objective is not finite");
     }
+    return DEAM_OK;
+}
+
+int deam_penalty(deam_ctx* ctx, const float* c, double* R, void* stream) {
+    CHECK_CTX(ctx);
+    if (!c || !R) return fail(DEAM_ERR_ARG, "c and R must not be NULL");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const deam_geometry& g = ctx->geo;
+    CK(deam::launch_penalty((const float2*)c, g.nx, g.ny, g.nz, (float)g.dx, (float)g.dy, (float)g.dz,
+                            (float)ctx->lambda, (float)ctx->delta, ctx->partial, ctx->n_fwd_blocks, s));
+    CK(deam::launch_sum_partials(ctx->partial, ctx->n_fwd_blocks, ctx->scal + 2, 0, s));
+    CK(cudaMemcpyAsync(R, ctx->scal + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
     return DEAM_OK;
 }
 

@@ -211,6 +211,12 @@ static int record_iteration(deam_batch* b, float* const* c, int plan) {
             if (b->bshape[cl] >= 0)
                 e = deam::launch_backward_batch(b->bshape[cl], desc(b, b->fshape, b->bshape[cl]),
                                                 b->bgrid[b->bshape[cl]], s);
+        for (int i = 0; i < b->n && e == cudaSuccess; ++i)  // regularised scans: the per-voxel solve
+            if (b->ctx[i]->lambda > 0.0) {
+                deam::BwdArgs B = b->hbargs[0][i];
+                B.img = (float2*)c[i];
+                e = deam::launch_reg_update(b->ctx[i]->G, B, s);
+            }
     } else {
         e = cudaEventRecord(b->fork, s);
         for (int i = 0; i < b->n && e == cudaSuccess && rc == DEAM_OK; ++i) {
@@ -235,7 +241,9 @@ static int record_iteration(deam_batch* b, float* const* c, int plan) {
             B.invZ = (float)(1.0 / x->Z);
             B.clamp_nonneg = x->clamp;
             B.skipped = x->skipped;
+            deam::set_penalty_args(x, B);
             if (e == cudaSuccess) e = deam::launch_backward(deam::BWD_UPDATE, x->slab, x->G, B, q);
+            if (e == cudaSuccess && B.sums) e = deam::launch_reg_update(x->G, B, q);
             if (e == cudaSuccess) e = cudaEventRecord(b->join[i], q);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->join[i], 0);
         }
@@ -417,6 +425,7 @@ int deam_batch_create(deam_ctx* const* ctxs, int n, int autotune, deam_batch** o
             a.invZ = (float)(1.0 / ctxs[i]->Z);
             a.clamp_nonneg = ctxs[i]->clamp;
             a.skipped = ctxs[i]->skipped;
+            deam::set_penalty_args(ctxs[i], a);
         }
         b->bgrid[bs] = sms * deam::backward_batch_blocks_per_sm(bs);
         if (off[n] > 0 && (b->bshape[cl] < 0 || deam::kBwdShapes[bs][1] == 16)) b->bshape[cl] = bs;  // default 16x8

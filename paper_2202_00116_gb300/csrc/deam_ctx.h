@@ -15,6 +15,7 @@ struct deam_ctx {
     int device = 0;
     double Z = 0.0, threshold = 0.0, mumax = 0.0;
     int clamp = 0;
+    double lambda = 0.0, delta = 1.0;  // penalty of Eqs. (6)-(7)
     bool has_data = false, mask_set = false, failed = false;
     long long nrays = 0, nvox = 0, skipped_last = 0;
     int n_fwd_blocks = 0, n_slabs = 0, slab = 16;
@@ -39,6 +40,7 @@ struct deam_ctx {
     unsigned long long* skipped = nullptr;
     float2* c_stage = nullptr;
     float2* coef = nullptr;  // deam_basis_images coefficients
+    float4* sums = nullptr;  // regularised c-step: backprojected sums per voxel (lambda > 0)
     // per-kernel timing of deam_iterate (deam_profile)
     bool prof = false;
     double prof_ms[4] = {0, 0, 0, 0};
@@ -52,4 +54,6 @@ int2 slab_view_range(const deam_geometry& g, int s, int slab);
 int build_layouts(deam_ctx* ctx, const float2* c, const float* m, int ones, cudaStream_t s);
 // Forward-kernel arguments bound to the context's buffers.
 FwdArgs fwd_args(deam_ctx* ctx);
+// Penalty fields of the backprojection arguments (lambda = 0: unregularised).
+void set_penalty_args(const deam_ctx* ctx, BwdArgs& B);
 }  // namespace deam

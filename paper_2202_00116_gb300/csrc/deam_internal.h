@@ -127,6 +127,13 @@ struct BwdArgs {
     float invZ;
     int clamp_nonneg;
     unsigned long long* skipped;  // update: count of unchanged (voxel, component) pairs
+    // regularised c-step (Eqs. 6-7), lambda > 0: the backprojection stores its
+    // per-voxel sums in `sums` and reg_update_kernel solves; neighbours' c^k are
+    // read from the projector layout volX, which holds c^k while the update runs
+    float4* sums;                 // [nvox] (b~_1, b~_2, delta_1, delta_2); nullptr: plain c-step
+    float lambda, delta, Z;
+    float pdx, pdy, pdz;          // voxel edges (mm) for the 1/distance weights
+    const float4* volX;
 };
 
 // Batched launch over many scans (deam_batch_*): per-scan descriptors in
@@ -173,6 +180,9 @@ cudaError_t launch_backward(int mode, int slab, const Geo& G, const BwdArgs& A, 
 cudaError_t launch_sum_partials(const double* partial, int n, double* out, int do_max, cudaStream_t s);
 cudaError_t launch_clamp_copy(const float* d, float* dt, long long n, cudaStream_t s);
 cudaError_t launch_mask_bits(uint8_t* m, long long n, int per_spectrum, cudaStream_t s);
+cudaError_t launch_reg_update(const Geo& G, const BwdArgs& A, cudaStream_t s);
+cudaError_t launch_penalty(const float2* c, int nx, int ny, int nz, float dx, float dy, float dz, float lambda,
+                           float delta, double* partial, int n_blocks, cudaStream_t s);
 cudaError_t launch_combine(const float2* c, long long nvox, const float2* ab, int n, float* out, cudaStream_t s);
 
 // Record an error message for deam_last_error() and return code (deam_api.cu).

@@ -227,6 +227,66 @@ __device__ __forceinline__ void pend_flush(float4* acc, int s, int tid, float4 x
     }
 }
 
+// ---- regularised c-step (Eqs. 6-7) --------------------------------------
+// phi(u) = delta^2 (|u|/delta - log(1 + |u|/delta)): phi' = u / (1 + |u|/delta),
+// phi'' = 1 / (1 + |u|/delta)^2.  For voxel x and component i the c-step
+// minimises over t the DEAM surrogate plus De Pierro's separable surrogate of
+// the pairwise penalty,
+//   G(t) = bh (t - ck) + (bt / Z) e^{-Z (t - ck)} + lambda sum_n w_n phi(2 t - m_n),
+// m_n = ck + ck of neighbour n.  G' increases; |phi'| < delta brackets its root.
+__device__ __forceinline__ float reg_solve(float ck, float bt, float bh, float Z, float lam, float delta,
+                                           const float* m, const float* w, int nn) {
+    float pmax = 0.f;
+    for (int n = 0; n < nn; ++n) pmax += 2.f * lam * w[n] * delta;
+    auto gprime = [&](float t, float* gpp) {
+        float gp = bh, g2 = 0.f;
+        if (bt > 0.f) {
+            const float e = bt * expf(-Z * (t - ck));
+            gp -= e;
+            g2 += Z * e;
+        }
+        for (int n = 0; n < nn; ++n) {
+            const float u = 2.f * t - m[n];
+            const float a = 1.f + fabsf(u) / delta;
+            gp += 2.f * lam * w[n] * (u / a);
+            g2 += 4.f * lam * w[n] / (a * a);
+        }
+        if (gpp) *gpp = g2;
+        return gp;
+    };
+    float lo, hi;
+    if (bt > 0.f) {
+        lo = ck - logf((bh + pmax) / bt) / Z;
+        const float b = bh - pmax;
+        if (b > 0.f) {
+            hi = ck - logf(b / bt) / Z;
+        } else {
+            hi = lo + 1.f;
+            for (int it = 0; it < 60 && gprime(hi, nullptr) <= 0.f; ++it) hi = lo + 2.f * (hi - lo);
+        }
+    } else {
+        lo = 1e30f;
+        hi = -1e30f;
+        for (int n = 0; n < nn; ++n) {
+            lo = fminf(lo, 0.5f * m[n]);
+            hi = fmaxf(hi, 0.5f * m[n]);
+        }
+    }
+    float t = 0.5f * (lo + hi);
+    for (int it = 0; it < 60; ++it) {
+        float g2;
+        const float gp = gprime(t, &g2);
+        if (gp > 0.f) hi = t;
+        else lo = t;
+        float tn = g2 > 0.f ? t - gp / g2 : 0.5f * (lo + hi);
+        if (!(tn > lo && tn < hi)) tn = 0.5f * (lo + hi);
+        const bool done = fabsf(tn - t) <= 1e-7f * (1.f + fabsf(t)) || hi - lo <= 1e-7f * (1.f + fabsf(t));
+        t = tn;
+        if (done) break;
+    }
+    return t;
+}
+
 // One (column tile, z-slab) of the gather backprojection: the work of one block.
 template <int MODE, int SLAB, int TX, int TY>
 __device__ __forceinline__ void bwd_tile(const Geo& G, const BwdArgs& A, float4* acc, int bx, int by, int slab) {
@@ -378,8 +438,12 @@ __device__ __forceinline__ void bwd_tile(const Geo& G, const BwdArgs& A, float4*
             A.img[vi] = make_float2(a.x, a.y);
             continue;
         }
-        // c-step: c_i <- c_i - (1/Z) ln(b^_i / b~_i) = c_i - (1/Z) log1p(delta_i / b~_i)
+        if (A.sums) {  // regularised c-step: reg_update_kernel finishes the update
+            A.sums[vi] = a;
+            continue;
+        }
         float2 c = A.img[vi];
+        // c-step: c_i <- c_i - (1/Z) ln(b^_i / b~_i) = c_i - (1/Z) log1p(delta_i / b~_i)
         float ratio;
         if (a.x > 0.f && (ratio = a.z / a.x) > -1.f) {
             c.x = fmaf(-log1pf(ratio), A.invZ, c.x);
@@ -555,6 +619,76 @@ __global__ void __launch_bounds__(256) sum_partials_kernel(const double* __restr
     if (threadIdx.x == 0) *out = sh[0];
 }
 
+// Regularised c-step over all voxels from the backprojected sums (b~_1, b~_2,
+// delta_1, delta_2) of every voxel; neighbours' c^k come from the projector
+// layout volX (element (ix', iz'+1, iy'+1) holds c(ix', iy', iz') in .xy), which
+// still holds c^k while c is updated in place.
+__global__ void reg_update_kernel(const Geo G, const BwdArgs A) {
+    const long long nvox = (long long)G.nx * G.ny * G.nz;
+    unsigned long long skipped = 0;
+    for (long long vi = (long long)blockIdx.x * blockDim.x + threadIdx.x; vi < nvox;
+         vi += (long long)gridDim.x * blockDim.x) {
+        const int ix = (int)(vi % G.nx), iy = (int)((vi / G.nx) % G.ny), iz = (int)(vi / ((long long)G.nx * G.ny));
+        const float4 a = A.sums[vi];
+        const float2 c = A.img[vi];
+        float m1[26], m2[26], w[26];
+        int nn = 0;
+        for (int oz = -1; oz <= 1; ++oz)
+            for (int oy = -1; oy <= 1; ++oy)
+                for (int ox = -1; ox <= 1; ++ox) {
+                    if (!ox && !oy && !oz) continue;
+                    const int jx = ix + ox, jy = iy + oy, jz = iz + oz;
+                    if (jx < 0 || jy < 0 || jz < 0 || jx >= G.nx || jy >= G.ny || jz >= G.nz) continue;
+                    const float4 e = __ldg(&A.volX[((long long)jx * (G.nz + 2) + jz + 1) * (G.ny + 1) + jy + 1]);
+                    m1[nn] = c.x + e.x;
+                    m2[nn] = c.y + e.y;
+                    const float px = ox * A.pdx, py = oy * A.pdy, pz = oz * A.pdz;
+                    w[nn] = rsqrtf(px * px + py * py + pz * pz);
+                    ++nn;
+                }
+        float2 cn = c;
+        const float bh1 = a.x + a.z, bh2 = a.y + a.w;
+        if ((a.x > 0.f && !(bh1 > 0.f)) || (!(a.x > 0.f) && nn == 0)) ++skipped;
+        else cn.x = reg_solve(c.x, a.x > 0.f ? a.x : 0.f, a.x > 0.f ? bh1 : 0.f, A.Z, A.lambda, A.delta, m1, w, nn);
+        if ((a.y > 0.f && !(bh2 > 0.f)) || (!(a.y > 0.f) && nn == 0)) ++skipped;
+        else cn.y = reg_solve(c.y, a.y > 0.f ? a.y : 0.f, a.y > 0.f ? bh2 : 0.f, A.Z, A.lambda, A.delta, m2, w, nn);
+        if (A.clamp_nonneg) {
+            cn.x = fmaxf(cn.x, 0.f);
+            cn.y = fmaxf(cn.y, 0.f);
+        }
+        A.img[vi] = cn;
+    }
+    if (skipped) atomicAdd(A.skipped, skipped);
+}
+
+// R(c) of Eqs. (6)-(7): per-block FP64 partial sums over voxels (each ordered
+// neighbour pair once, as printed).
+__global__ void __launch_bounds__(kFwdThreads) penalty_kernel(const float2* __restrict__ c, int nx, int ny, int nz,
+                                                              float dx, float dy, float dz, float lam, float delta,
+                                                              double* __restrict__ partial) {
+    const long long nvox = (long long)nx * ny * nz;
+    double acc = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nvox;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int ix = (int)(i % nx), iy = (int)((i / nx) % ny), iz = (int)(i / ((long long)nx * ny));
+        const float2 v = c[i];
+        for (int oz = -1; oz <= 1; ++oz)
+            for (int oy = -1; oy <= 1; ++oy)
+                for (int ox = -1; ox <= 1; ++ox) {
+                    if (!ox && !oy && !oz) continue;
+                    const int jx = ix + ox, jy = iy + oy, jz = iz + oz;
+                    if (jx < 0 || jy < 0 || jz < 0 || jx >= nx || jy >= ny || jz >= nz) continue;
+                    const float2 u = c[((long long)jz * ny + jy) * nx + jx];
+                    const float px = ox * dx, py = oy * dy, pz = oz * dz;
+                    const float w = rsqrtf(px * px + py * py + pz * pz);
+                    const float a1 = fabsf(v.x - u.x) / delta, a2 = fabsf(v.y - u.y) / delta;
+                    acc += (double)(w * delta * delta) * ((double)(a1 - log1pf(a1)) + (double)(a2 - log1pf(a2)));
+                }
+    }
+    const double b = block_reduce<kFwdThreads, double>(acc * (double)lam, false);
+    if (threadIdx.x == 0) partial[blockIdx.x] = b;
+}
+
 // out[e][x] = a_e c_1(x) + b_e c_2(x) for n coefficient pairs: virtual
 // monoenergetic images (a, b) = (mu_1(E), mu_2(E)) and spectrum-weighted
 // averages of them.  HBM-bound: reads c once per voxel, writes n floats.
@@ -712,6 +846,17 @@ cudaError_t launch_inplane_table(const Geo& G, float4* ip4, float* ipL, cudaStre
 
 cudaError_t launch_sum_partials(const double* partial, int n, double* out, int do_max, cudaStream_t s) {
     sum_partials_kernel<<<1, 256, 0, s>>>(partial, n, out, do_max);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reg_update(const Geo& G, const BwdArgs& A, cudaStream_t s) {
+    reg_update_kernel<<<grid_for((long long)G.nx * G.ny * G.nz, 128), 128, 0, s>>>(G, A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_penalty(const float2* c, int nx, int ny, int nz, float dx, float dy, float dz, float lambda,
+                           float delta, double* partial, int n_blocks, cudaStream_t s) {
+    penalty_kernel<<<n_blocks, kFwdThreads, 0, s>>>(c, nx, ny, nz, dx, dy, dz, lambda, delta, partial);
     return cudaGetLastError();
 }
 
