@@ -403,6 +403,183 @@ def run_batch(args):
     batch.close()
     return 0
 
+def _timed_iterate(g, c, n, stream):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    h = g.iterate(c, n)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return h, e0.elapsed_time(e1)
+
+
+def run_compare(args):
+    """The default (mixed-precision) DEAM, its adjoint (gradient) form and its
+    batched form, each next to the plain-FP32 GPU DEAM (deam_options.precision
+    = 1: uncompensated FP32 spectral sums and FP32 objective accumulation):
+
+    precision  at 512x512x64 helical: iterations/s of both; payload error on
+               seeded sampled rays against the FP64 oracle; the FP32 objective's
+               deviation from the FP64-reduced one; at the 2D fan case, each
+               output's error after 10 iterations against the full oracle run.
+    adjoint    at 256x256x32 helical: DEAM iterations against Barzilai-Borwein
+               gradient descent on the same objective (gradients from the
+               adjoint kernel), compared at the same objective value.
+    batched    24 seeded scans of uneven size: one batch against scan-by-scan
+               plain-FP32 and mixed deam_iterate.
+    """
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2202_00116_gb300 as pkg
+    import synth
+    from paper_2202_00116_gb300 import build, solvers
+    build.build()
+    oracle.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream(dev)
+    rng = np.random.default_rng(11)
+    out = {}
+
+    def rel(a, b):
+        a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+    # precision, full size
+    case, d, mask, c0 = build_workload("c2", dev)
+    O = oracle.from_case(case)
+    rays = np.sort(rng.choice(case.geo.n_rays, size=4096, replace=False))
+    _, _, po, fo = O.ray_model(c0.cpu().double().numpy(), d.cpu().double().numpy(), mask.cpu().numpy(), rays)
+    prec = {}
+    for p in ("mixed", "fp32"):
+        g = pkg.from_case(case, precision=p)
+        g.set_data(d)
+        g.set_metal_mask(mask, "ray")
+        pay, F = g.ray_terms(c0)
+        pg = pay.reshape(-1, 4)[torch.from_numpy(rays).to(dev)].cpu().double().numpy()
+        c = c0.clone()
+        g.iterate(c, args.warmup)
+        h, ms = _timed_iterate(g, c, args.steps, stream)
+        prec[p] = {"it_per_s": args.steps / (ms / 1e3), "ms_per_it": ms / args.steps, "objective_at_c0": F,
+                   "sampled_rays_rel_l2": {"B_tilde": rel(pg[:, :2], po[:, :2]),
+                                           "B_hat": rel(pg[:, :2] + pg[:, 2:], po[:, 2:])},
+                   "image": c}
+        g.close()
+    prec["fp32"]["objective_rel_dev_from_fp64_reduction"] = abs(
+        prec["fp32"]["objective_at_c0"] - prec["mixed"]["objective_at_c0"]) / prec["mixed"]["objective_at_c0"]
+    prec["image_rel_l2_fp32_vs_mixed_after_iterations"] = rel(prec["fp32"].pop("image").cpu().numpy(),
+                                                              prec["mixed"].pop("image").cpu().numpy())
+    del d, mask, c0
+    case, d, mask, c0 = build_workload("c0", dev)
+    O = oracle.from_case(case)
+    c_ref, h_ref, _ = O.iterate(c0.cpu().double().numpy(), d.cpu().double().numpy(), mask.cpu().numpy(),
+                                n_iter=10)
+    for p in ("mixed", "fp32"):
+        g = pkg.from_case(case, precision=p)
+        g.set_data(d)
+        g.set_metal_mask(mask, "ray")
+        c = c0.clone()
+        h = g.iterate(c, 10)
+        prec[p]["fan2d_10_iterations_vs_oracle"] = {
+            "image_rel_l2": rel(c.cpu().numpy(), c_ref),
+            "objective_history_max_rel": float(np.max(np.abs(h - h_ref) / h_ref))}
+        g.close()
+    out["precision"] = prec
+
+    # adjoint form against DEAM, 256x256x32 helical
+    case, d, mask, c0 = build_workload("c1", dev)
+    runs = {}
+    for p in ("fp32", "mixed"):
+        g = pkg.from_case(case, precision=p)
+        g.set_data(d)
+        g.set_metal_mask(mask, "ray")
+        c = c0.clone()
+        g.iterate(c.clone(), 2)
+        h, ms = _timed_iterate(g, c, 50, stream)
+        runs[p] = (np.append(h, g.objective(c)), ms / 50)
+        if p == "mixed":
+            gm = g
+        else:
+            g.close()
+    cg = c0.clone()
+    gm.gradient(cg.clone())
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(5):
+        gm.gradient(cg)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_grad = e0.elapsed_time(e1) / 5
+    gd = solvers.gradient_descent(gm, cg, 200)
+    hf, ms_f = runs["fp32"]
+    target = hf[20]   # the plain-FP32 DEAM's objective after 20 iterations
+    reach = np.nonzero(gd["objective"][1:] <= target)[0]
+    adj = {"workload": "256x256x32 helical, 16x672, 3480 views, 2 x 60 bins",
+           "deam_fp32": {"ms_per_iteration": ms_f, "objective": {k: float(hf[k]) for k in (0, 1, 5, 10, 20, 50)}},
+           "deam_mixed": {"ms_per_iteration": runs["mixed"][1],
+                          "objective": {k: float(runs["mixed"][0][k]) for k in (0, 1, 5, 10, 20, 50)}},
+           "gradient_descent_bb": {"ms_per_gradient": ms_grad, "steps": len(gd["objective"]) - 1,
+                                   "evaluations": int(gd["evaluations"][-1]) if gd["evaluations"] else 0,
+                                   "seconds": gd["seconds"][-1] if gd["seconds"] else 0.0,
+                                   "objective": {k: float(gd["objective"][k]) for k in (0, 1, 10, 50, 100, 200)
+                                                 if k < len(gd["objective"])}},
+           "same_accuracy": {"target": "objective of plain-FP32 DEAM after 20 iterations",
+                             "deam_fp32_seconds": 20 * ms_f / 1e3,
+                             "gradient_descent_steps": int(reach[0]) + 1 if reach.size else None,
+                             "gradient_descent_seconds": gd["seconds"][int(reach[0])] if reach.size else None}}
+    gm.close()
+    out["adjoint"] = adj
+    del d, mask, c0
+
+    # batched form
+    cases = synth.make_batch_cases(args.batch_scans)
+    bat = {}
+    for p in ("fp32", "mixed"):
+        scans, imgs = [], []
+        for cs in cases:
+            dd, metal = synth.measure(cs, device=dev, seed=1)
+            truth, _ = synth.voxelize(cs, device=dev)
+            g = pkg.from_case(cs, precision=p)
+            g.set_data(dd)
+            g.set_metal_mask((metal >= cs.metal_threshold).to(torch.uint8), "ray")
+            scans.append(g)
+            imgs.append(synth.initial_image(cs, truth).to(dev))
+            del dd, metal, truth
+        cs_ = [c.clone() for c in imgs]
+        for g, c in zip(scans, cs_):
+            g.iterate(c, 1)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for g, c in zip(scans, cs_):
+            g.iterate(c, args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        bat[f"sequential_{p}"] = {"it_per_s": args.steps / (e0.elapsed_time(e1) / 1e3)}
+        if p == "mixed":
+            batch = pkg.DeamBatch(scans, autotune=True)
+            cb = [c.clone() for c in imgs]
+            batch.iterate(cb, 2)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            batch.iterate(cb, args.steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            bat["batched_mixed"] = {"it_per_s": args.steps / (e0.elapsed_time(e1) / 1e3),
+                                    "plan": batch.info()["plan"]}
+            batch.close()
+        for g in scans:
+            g.close()
+    bat["scans"] = len(cases)
+    out["batched"] = bat
+    line = {"metric": "comparison with the plain-FP32 GPU DEAM", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "data": "synthetic", "comparisons": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
 
 def main():
     ap = argparse.ArgumentParser()
@@ -418,6 +595,8 @@ def main():
     args = ap.parse_args()
     if args.config == "batch":
         return run_batch(args)
+    if args.config == "compare":
+        return run_compare(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -102,7 +102,11 @@ typedef struct deam_options {
     double penalty_lambda;  /* lambda of Eq. (6); 0 (default): unregularised MAR-DEAM */
     double penalty_delta;   /* delta of Eq. (7) (> 0 when lambda > 0) */
     int clamp_nonneg;       /* 1: clamp c_i >= 0 after each c-step (the paper is silent; default 0) */
-    int reserved[7];        /* zero */
+    int precision;          /* 0 (default): spectral sums in compensated FP32 and the objective in FP64;
+                               1: plain FP32 sums and FP32 objective accumulation (for comparison).
+                               Projection sampling is FP32 either way.  A batch holding a context
+                               with 1 runs its per-scan plan only (the persistent plan has only 0). */
+    int reserved[6];        /* zero */
 } deam_options;
 
 typedef struct deam_ctx deam_ctx;

@@ -48,7 +48,8 @@ class deam_basis(C.Structure):
 
 class deam_options(C.Structure):
     _fields_ = [("metal_threshold", C.c_double), ("Z", C.c_double), ("penalty_lambda", C.c_double),
-                ("penalty_delta", C.c_double), ("clamp_nonneg", C.c_int), ("reserved", C.c_int * 7)]
+                ("penalty_delta", C.c_double), ("clamp_nonneg", C.c_int), ("precision", C.c_int),
+                ("reserved", C.c_int * 6)]
 
 
 class DeamError(RuntimeError):
@@ -123,7 +124,7 @@ class Deam:
     """
 
     def __init__(self, geo, I0, mu, bowtie=None, energies=None, metal_threshold=0.0, Z=0.0,
-                 clamp_nonneg=False, penalty_lambda=0.0, penalty_delta=1.0, device=None):
+                 clamp_nonneg=False, penalty_lambda=0.0, penalty_delta=1.0, precision="mixed", device=None):
         import torch
         self.torch = torch
         if device is None:
@@ -143,8 +144,10 @@ class Deam:
         sp = deam_spectra(nE, self._E.ctypes.data_as(P) if self._E is not None else P(),
                           self._I0.ctypes.data_as(P), self._bow.ctypes.data_as(P) if self._bow is not None else P())
         ba = deam_basis(self._mu.shape[1], self._mu.ctypes.data_as(P))
+        if precision not in ("mixed", "fp32"):
+            raise ValueError("precision is 'mixed' (compensated FP32 sums, FP64 objective) or 'fp32'")
         op = deam_options(float(metal_threshold), float(Z), float(penalty_lambda), float(penalty_delta),
-                          int(bool(clamp_nonneg)))
+                          int(bool(clamp_nonneg)), 1 if precision == "fp32" else 0)
         h = C.c_void_p()
         self._h = None
         if torch.cuda.is_available():

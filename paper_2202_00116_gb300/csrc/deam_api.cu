@@ -217,6 +217,11 @@ int deam_init(const deam_geometry* geom, const deam_spectra* spectra, const deam
     ctx->nrays = (long long)g.n_views * g.n_rows * g.n_channels;
     ctx->nvox = (long long)g.nx * g.ny * g.nz;
     ctx->clamp = o.clamp_nonneg ? 1 : 0;
+    if (o.precision != 0 && o.precision != 1) {
+        delete ctx;
+        return fail(DEAM_ERR_ARG, "precision must be 0 (compensated) or 1 (plain FP32)");
+    }
+    ctx->fwd_mode = o.precision == 1 ? deam::FWD_DEAM_F32 : deam::FWD_DEAM;
     ctx->lambda = o.penalty_lambda;
     ctx->delta = o.penalty_lambda > 0.0 ? o.penalty_delta : 1.0;
     ctx->threshold = o.metal_threshold > 0.0 ? o.metal_threshold
@@ -479,7 +484,7 @@ static int ray_terms(deam_ctx* ctx, const float2* c, float4* payload, double* F,
     A.dt = ctx->dt;
     A.mask = ctx->mask_set ? ctx->mask : nullptr;
     A.payload = payload;
-    CK(deam::launch_forward(deam::FWD_DEAM, ctx->G, ctx->S, A, ctx->n_fwd_blocks, s));
+    CK(deam::launch_forward(ctx->fwd_mode, ctx->G, ctx->S, A, ctx->n_fwd_blocks, s));
     CK(deam::launch_sum_partials(ctx->partial, ctx->n_fwd_blocks, F_dev, 0, s));
     if (F) {
         CK(cudaMemcpyAsync(F, F_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -551,7 +556,7 @@ int deam_iterate(deam_ctx* ctx, float* c, int n_iter, double* hist, void* stream
         int rc = build_layouts(ctx, cd, nullptr, 0, s);
         if (rc != DEAM_OK) return rc;
         if (e) CK(cudaEventRecord(e[1], s));
-        CK(deam::launch_forward(deam::FWD_DEAM, ctx->G, ctx->S, A, ctx->n_fwd_blocks, s));
+        CK(deam::launch_forward(ctx->fwd_mode, ctx->G, ctx->S, A, ctx->n_fwd_blocks, s));
         if (e) CK(cudaEventRecord(e[2], s));
         CK(deam::launch_sum_partials(ctx->partial, ctx->n_fwd_blocks, ctx->hist + it, 0, s));
         CK(cudaMemsetAsync(ctx->skipped, 0, sizeof(unsigned long long), s));

@@ -54,6 +54,7 @@ struct deam_batch {
     float tune_fwd_ms[kNF] = {0, 0, 0}, tune_bwd_ms[kNB] = {0, 0, 0, 0, 0, 0};
     int fgrid[kNF] = {}, bgrid[kNB] = {};
     int plan = 0;                    // 0: persistent launches over all scans, 1: per-scan launches on graph branches
+    int min_plan = 0;                // 1 when a scan asks for the plain-FP32 forward (plan 0 has only the compensated one)
     float tune_plan_ms[2] = {0, 0};
     long long* soff = nullptr;       // [n][2] = {0, forward blocks of scan i}: per-scan objective ranges
     std::vector<cudaStream_t> br;    // graph branches of the per-scan plan
@@ -229,7 +230,7 @@ static int record_iteration(deam_batch* b, float* const* c, int plan) {
             A.dt = x->dt;
             A.mask = x->mask_set ? x->mask : nullptr;
             A.payload = x->payload;
-            e = deam::launch_forward(deam::FWD_DEAM, x->G, x->S, A, x->n_fwd_blocks, q);
+            e = deam::launch_forward(x->fwd_mode, x->G, x->S, A, x->n_fwd_blocks, q);
             if (e == cudaSuccess)
                 e = deam::launch_sum_ranges(x->partial, b->soff + 2 * i, 1, b->hist + (size_t)i * b->hist_cap,
                                             b->counter, b->hist_cap, q);
@@ -298,8 +299,8 @@ static int tune_plan(deam_batch* b) {
     BK(cudaEventCreate(&e0));
     BK(cudaEventCreate(&e1));
     float best = 1e30f;
-    int best_plan = 0;
-    for (int plan = 0; plan < 2; ++plan) {
+    int best_plan = b->min_plan;
+    for (int plan = b->min_plan; plan < 2; ++plan) {
         rc = capture(b, sc.data(), plan);
         if (rc != DEAM_OK) return rc;
         BK(cudaMemsetAsync(b->counter, 0, sizeof(int), b->cs));
@@ -349,6 +350,9 @@ int deam_batch_create(deam_ctx* const* ctxs, int n, int autotune, deam_batch** o
     b->device = dev;
     b->autotune = autotune ? 1 : 0;
     b->ctx.assign(ctxs, ctxs + n);
+    for (int i = 0; i < n; ++i)
+        if (ctxs[i]->fwd_mode != deam::FWD_DEAM) b->min_plan = 1;
+    b->plan = b->min_plan;
     auto bail = [&](int rc) {
         std::string m = deam_last_error();
         free_batch(b);

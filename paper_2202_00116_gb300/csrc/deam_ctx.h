@@ -16,6 +16,7 @@ struct deam_ctx {
     double Z = 0.0, threshold = 0.0, mumax = 0.0;
     int clamp = 0;
     double lambda = 0.0, delta = 1.0;  // penalty of Eqs. (6)-(7)
+    int fwd_mode = deam::FWD_DEAM;     // FWD_DEAM_F32 for the plain-FP32 variant
     bool has_data = false, mask_set = false, failed = false;
     long long nrays = 0, nvox = 0, skipped_last = 0;
     int n_fwd_blocks = 0, n_slabs = 0, slab = 16;

@@ -66,11 +66,27 @@ __device__ __forceinline__ T block_reduce(T v, bool is_max) {
 // Spectral sums of one ray for both spectra: g_j = sum_E I0_j q~, S_ij = sum_E
 // mu_i I0_j q~ with q~ = 2^(-mu'.l) (bowtie applied by the caller).  Bins are
 // summed in blocks of 8 in FP32, block partials are added with compensation.
-template <bool NEED_S>
+// COMP = false: plain FP32 sums, bin after bin (the uncompensated variant).
+template <bool NEED_S, bool COMP = true>
 __device__ __forceinline__ void spectral_sums(const Spec& S, float l1, float l2, float& gl, float& gh,
                                               float& s1l, float& s2l, float& s1h, float& s2h) {
     float cgl = 0.f, cgh = 0.f, c1l = 0.f, c2l = 0.f, c1h = 0.f, c2h = 0.f;
     gl = gh = s1l = s2l = s1h = s2h = 0.f;
+    if (!COMP) {
+        for (int e = S.e_lo; e < S.e_hi; ++e) {
+            const float ex = ex2_approx(-fmaf(S.mu1l2[e], l1, S.mu2l2[e] * l2));
+            const float ql = S.i0l[e] * ex, qh = S.i0h[e] * ex;
+            gl += ql;
+            gh += qh;
+            if (NEED_S) {
+                s1l = fmaf(S.mu1[e], ql, s1l);
+                s2l = fmaf(S.mu2[e], ql, s2l);
+                s1h = fmaf(S.mu1[e], qh, s1h);
+                s2h = fmaf(S.mu2[e], qh, s2h);
+            }
+        }
+        return;
+    }
     for (int e0 = S.e_lo; e0 < S.e_hi; e0 += 8) {
         float pgl = 0.f, pgh = 0.f, p1l = 0.f, p2l = 0.f, p1h = 0.f, p2h = 0.f;
         const int n = min(8, S.e_hi - e0);

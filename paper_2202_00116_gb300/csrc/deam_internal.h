@@ -103,7 +103,9 @@ __device__ __forceinline__ float row_fz(const InPlane& ip, float sigma_z, float 
 // kernel launchers (deam_kernels.cu)
 // ---------------------------------------------------------------------------
 enum BwdMode { BWD_ADJOINT = 0, BWD_UPDATE = 1, BWD_GRADIENT = 2 };
-enum FwdMode { FWD_LINE = 0, FWD_LINE_G = 1, FWD_DEAM = 2, FWD_MASK = 3, FWD_MAX = 4, FWD_COUNT = 5 };
+// FWD_DEAM_F32: FWD_DEAM with plain FP32 spectral sums and FP32 objective
+// accumulation (the uncompensated variant, for comparison)
+enum FwdMode { FWD_LINE = 0, FWD_LINE_G = 1, FWD_DEAM = 2, FWD_MASK = 3, FWD_MAX = 4, FWD_COUNT = 5, FWD_DEAM_F32 = 6 };
 
 struct FwdArgs {
     const float4* volX;   // [nx][nz+2][ny+1] q-paired layout for x-dominant rays

@@ -116,9 +116,9 @@ __device__ __forceinline__ double fwd_ray(const Geo& G, const Spec& S, const Fwd
         if (A.l_out) A.l_out[y] = make_float2(l1, l2);
         A.g_out[y] = gl * bk;
         A.g_out[nrays + y] = gh * bk;
-    } else {  // FWD_DEAM
+    } else {  // FWD_DEAM, FWD_DEAM_F32
         float gl, gh, s1l, s2l, s1h, s2h;
-        spectral_sums<true>(S, l1, l2, gl, gh, s1l, s2l, s1h, s2h);
+        spectral_sums<true, MODE == FWD_DEAM>(S, l1, l2, gl, gh, s1l, s2l, s1h, s2h);
         const float bk = A.bowtie ? __ldg(&A.bowtie[k]) : 1.f;
         gl *= bk; gh *= bk; s1l *= bk; s2l *= bk; s1h *= bk; s2h *= bk;
         float4 P = make_float4(s1l + s1h, s2l + s2h, 0.f, 0.f);
@@ -179,16 +179,21 @@ __host__ __device__ __forceinline__ long long ray_tiles(const Geo& G) {
 template <int MODE>
 __global__ void __launch_bounds__(kFwdThreads) fwd_kernel(const Geo G, const Spec S, const FwdArgs A) {
     double red = 0.0;  // FWD_DEAM: objective of this thread's rays; FWD_MAX: max l_1
+    float redf = 0.f;  // FWD_DEAM_F32: the same in FP32
     const long long ntiles = ray_tiles<kTileR, kTileV>(G);
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
         int v, r, k;
         if (!ray_of_tile<kTileR, kTileV>(G, t, v, r, k)) continue;
         const double o = fwd_ray<MODE>(G, S, A, v, r, k);
-        red = MODE == FWD_MAX ? fmax(red, o) : red + o;
+        if (MODE == FWD_DEAM_F32) redf += (float)o;
+        else red = MODE == FWD_MAX ? fmax(red, o) : red + o;
     }
     if (MODE == FWD_DEAM || MODE == FWD_MAX || MODE == FWD_COUNT) {
         const double b = block_reduce<kFwdThreads, double>(red, MODE == FWD_MAX);
         if (threadIdx.x == 0) A.partial[blockIdx.x] = b;
+    } else if (MODE == FWD_DEAM_F32) {
+        const float b = block_reduce<kFwdThreads, float>(redf, false);
+        if (threadIdx.x == 0) A.partial[blockIdx.x] = (double)b;
     }
 }
 
@@ -747,6 +752,7 @@ cudaError_t launch_forward(int mode, const Geo& G, const Spec& S, const FwdArgs&
         case FWD_MASK: fwd_kernel<FWD_MASK><<<n_blocks, kFwdThreads, 0, s>>>(G, S, A); break;
         case FWD_MAX: fwd_kernel<FWD_MAX><<<n_blocks, kFwdThreads, 0, s>>>(G, S, A); break;
         case FWD_COUNT: fwd_kernel<FWD_COUNT><<<n_blocks, kFwdThreads, 0, s>>>(G, S, A); break;
+        case FWD_DEAM_F32: fwd_kernel<FWD_DEAM_F32><<<n_blocks, kFwdThreads, 0, s>>>(G, S, A); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

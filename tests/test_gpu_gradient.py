@@ -106,3 +106,22 @@ def test_autograd_function_and_descent(pkg):
     xd = c0.clone().cuda()
     hist = gpu.iterate(xd, 5)
     assert np.all(np.diff(hist) < 0)
+
+
+def test_gradient_solver_is_monotone_and_trails_deam(pkg):
+    # Barzilai-Borwein descent on the adjoint kernel's gradient never raises F
+    # (the monotone safeguard), and each accepted step lowers it; DEAM's
+    # majorise-minimise steps also decrease F (Sec. 2.3).  Both start from c0.
+    from paper_2202_00116_gb300 import solvers
+    case, d, mask, c0 = _case("t3d")
+    gpu = pkg.from_case(case)
+    gpu.set_data(d.cuda())
+    gpu.set_metal_mask(mask.cuda(), "ray")
+    c = c0.clone().cuda()
+    res = solvers.gradient_descent(gpu, c, 30)
+    F = res["objective"]
+    assert len(F) >= 2 and np.all(np.diff(F) <= 0) and F[-1] < F[0]
+    assert F[-1] == pytest.approx(gpu.objective(c), rel=1e-12)
+    assert np.all(np.diff(res["evaluations"]) >= 1)
+    h = gpu.iterate(c0.clone().cuda(), 10)
+    assert np.all(np.diff(h) < 0) and h[0] == pytest.approx(F[0], rel=1e-12)
