@@ -180,6 +180,16 @@ int deam_objective(deam_ctx *ctx, const float *c, double *out, void *stream);
  * Needs deam_set_data.  Deterministic. */
 int deam_gradient(deam_ctx *ctx, const float *c, float *grad, double *F, void *stream);
 
+/* The two backprojected sums of the c-step (Sec. 2.3 update, derived from
+ * Eqs. 5 and 8-11) at c, without applying it: sums (device float32
+ * [nz][ny][nx][4], overwritten) receives per voxel (b~_1, b~_2, delta_1,
+ * delta_2), b~_i = sum_{y,E} h mu_i q and delta_i = b^_i - b~_i (= dF/dc_i).
+ * The c-step would be c_i - (1/Z) log1p(delta_i / b~_i); -delta_i / (Z b~_i)
+ * is the diagonally preconditioned gradient step it approximates.  *F (host,
+ * may be NULL) receives F(c); *Z (host, may be NULL) the context's Z.  Needs
+ * deam_set_data.  Deterministic. */
+int deam_backprojected_sums(deam_ctx *ctx, const float *c, float *sums, double *F, double *Z, void *stream);
+
 /* Linear images of the basis components (Sec. 3): out[e] = a_e c_1 + b_e c_2 for
  * n coefficient pairs coef[2e] = a_e, coef[2e+1] = b_e (host, 1 <= n <= 256).
  * With (a_e, b_e) = (mu_1(E_e), mu_2(E_e)) these are virtual monoenergetic

@@ -61,7 +61,8 @@ class DeamError(RuntimeError):
 _lib = None
 EXPORTS = ["deam_init", "deam_set_data", "deam_set_metal_mask", "deam_get_metal_mask", "deam_forward",
            "deam_backproject", "deam_ray_terms", "deam_iterate", "deam_objective", "deam_info",
-           "deam_gradient", "deam_penalty", "deam_basis_images", "deam_count_samples", "deam_profile", "deam_kernel_times", "deam_batch_create",
+           "deam_gradient", "deam_backprojected_sums", "deam_penalty", "deam_basis_images", "deam_count_samples",
+           "deam_profile", "deam_kernel_times", "deam_batch_create",
            "deam_batch_iterate", "deam_batch_info", "deam_batch_destroy", "deam_objective_noalloc",
            "deam_destroy", "deam_last_error"]
 
@@ -87,6 +88,7 @@ def lib():
             "deam_objective": [vp, vp, pd, vp],
             "deam_info": [vp, pd, C.POINTER(C.c_longlong)],
             "deam_gradient": [vp, vp, vp, pd, vp],
+            "deam_backprojected_sums": [vp, vp, vp, pd, pd, vp],
             "deam_basis_images": [vp, vp, pd, i, vp, vp],
             "deam_penalty": [vp, vp, pd, vp],
             "deam_count_samples": [vp, C.POINTER(C.c_longlong), vp],
@@ -269,6 +271,18 @@ class Deam:
         _check(lib().deam_gradient(self._h, self._arg(c, self.img_shape, torch.float32),
                                    self._arg(out, self.img_shape, torch.float32), C.byref(F), self._stream()))
         return out, F.value
+
+    def backprojected_sums(self, c, out=None):
+        """(sums float32 [nz, ny, nx, 4] = (b~1, b~2, delta1, delta2), F(c), Z):
+        the c-step's backprojected sums at c without the update; delta = dF/dc."""
+        torch = self.torch
+        if out is None:
+            out = torch.empty(self.img_shape[:3] + (4,), dtype=torch.float32, device=self.device)
+        F, Z = C.c_double(), C.c_double()
+        _check(lib().deam_backprojected_sums(self._h, self._arg(c, self.img_shape, torch.float32),
+                                             self._arg(out, self.img_shape[:3] + (4,), torch.float32),
+                                             C.byref(F), C.byref(Z), self._stream()))
+        return out, F.value, Z.value
 
     def penalty(self, c):
         """R(c) of Eqs. (6)-(7) with the context's lambda and delta."""

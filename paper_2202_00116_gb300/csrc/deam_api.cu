@@ -589,6 +589,28 @@ int deam_iterate(deam_ctx* ctx, float* c, int n_iter, double* hist, void* stream
     return DEAM_OK;
 }
 
+int deam_backprojected_sums(deam_ctx* ctx, const float* c, float* sums, double* F, double* Z, void* stream) {
+    CHECK_CTX(ctx);
+    if (!c || !sums) return fail(DEAM_ERR_ARG, "c and sums must not be NULL");
+    if (!ctx->has_data) return fail(DEAM_ERR_STATE, "deam_set_data has not been called");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = ray_terms(ctx, (const float2*)c, ctx->payload, nullptr, ctx->scal, s);
+    if (rc != DEAM_OK) return rc;
+    deam::BwdArgs B{};
+    B.payload = ctx->payload;
+    B.slab_views = ctx->slab_views;
+    B.sums = (float4*)sums;  // the c-step's backprojection, stopped before the update
+    CK(deam::launch_backward(deam::BWD_UPDATE, ctx->slab, ctx->G, B, s));
+    if (Z) *Z = ctx->Z;
+    if (F) {
+        CK(cudaMemcpyAsync(F, ctx->scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (!isfinite(*F)) return fail(DEAM_ERR_NUMERIC, "objective is not finite");
+    }
+    return DEAM_OK;
+}
+
 int deam_gradient(deam_ctx* ctx, const float* c, float* grad, double* F, void* stream) {
     CHECK_CTX(ctx);
     if (!c || !grad) return fail(DEAM_ERR_ARG, "c and grad must not be NULL");

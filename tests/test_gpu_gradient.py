@@ -125,3 +125,48 @@ def test_gradient_solver_is_monotone_and_trails_deam(pkg):
     assert np.all(np.diff(res["evaluations"]) >= 1)
     h = gpu.iterate(c0.clone().cuda(), 10)
     assert np.all(np.diff(h) < 0) and h[0] == pytest.approx(F[0], rel=1e-12)
+
+
+@pytest.mark.parametrize("name", ["t3d", "c0"])
+def test_backprojected_sums_match_oracle(pkg, name):
+    # (b~, delta = b^ - b~) of the c-step at c0 against the oracle's FP64 sums;
+    # delta equals deam_gradient bitwise (same payload, same accumulation
+    # order), and applying the c-step to them gives one deam_iterate step.
+    import oracle
+    case, d, mask, c0 = _case(name)
+    gpu = pkg.from_case(case)
+    gpu.set_data(d.cuda())
+    gpu.set_metal_mask(mask.cuda(), "ray")
+    sums, F, Z = gpu.backprojected_sums(c0.cuda())
+    O = oracle.from_case(case)
+    bt, bh, Fo = O.backprojected_sums(c0.double().numpy(), d.double().numpy(), mask.numpy())
+    s = sums.cpu().double().numpy()
+    assert _rel(s[..., :2], bt) < 1e-5
+    assert np.linalg.norm(s[..., 2:] - (bh - bt)) / np.linalg.norm(bh) < 1e-5
+    assert F == pytest.approx(Fo, rel=1e-5)
+    assert Z == pytest.approx(O.normaliser(), rel=1e-5)
+    g, Fg = gpu.gradient(c0.cuda())
+    assert torch.equal(g, sums[..., 2:].contiguous()) and Fg == F
+    c = c0.clone().cuda()
+    gpu.iterate(c, 1)
+    b, dl = sums[..., :2].double(), sums[..., 2:].double()
+    ok = (b > 0) & (dl / b.clamp_min(1e-300) > -1)
+    step = torch.where(ok, -torch.log1p(dl / torch.where(ok, b, torch.ones_like(b))) / Z, torch.zeros_like(b))
+    ref = c0.cuda().double() + step
+    assert float((c.double() - ref).abs().max()) <= 1e-6 * float(ref.abs().max()) + 1e-7
+
+
+def test_preconditioned_gradient_solver(pkg):
+    # the 1/(Z b~) preconditioned descent (DEAM's c-step is its exact-surrogate
+    # form) keeps F monotone under the BB steps and the halving safeguard
+    from paper_2202_00116_gb300 import solvers
+    case, d, mask, c0 = _case("t3d")
+    gpu = pkg.from_case(case)
+    gpu.set_data(d.cuda())
+    gpu.set_metal_mask(mask.cuda(), "ray")
+    c = c0.clone().cuda()
+    res = solvers.gradient_descent(gpu, c, 20, precondition=True)
+    F = res["objective"]
+    assert len(F) >= 2 and np.all(np.diff(F) <= 0) and F[-1] < F[0]
+    assert F[0] == pytest.approx(gpu.objective(c0.cuda()), rel=1e-12)
+    assert F[-1] == pytest.approx(gpu.objective(c), rel=1e-12)
