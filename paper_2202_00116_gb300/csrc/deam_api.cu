@@ -233,7 +233,7 @@ int deam_init(const deam_geometry* geom, const deam_spectra* spectra, const deam
     const long long ntiles = (long long)((g.n_channels + deam::kTileK - 1) / deam::kTileK) *
                              ((g.n_rows + deam::kTileR - 1) / deam::kTileR) *
                              ((g.n_views + deam::kTileV - 1) / deam::kTileV);
-    ctx->n_fwd_blocks = (int)std::min<long long>(ntiles, (long long)sms * 8);
+    ctx->n_fwd_blocks = (int)std::min<long long>(ntiles, (long long)sms * deam::forward_blocks_per_sm());
 
     // ---- geometry tables (double on the host, rounded once to float) ----
     const double X0 = g.cx - (g.nx - 1) / 2.0 * g.dx, Y0 = g.cy - (g.ny - 1) / 2.0 * g.dy,

@@ -176,6 +176,7 @@ cudaError_t launch_counter_inc(int* counter, cudaStream_t s);
 cudaError_t launch_inplane_table(const Geo& G, float4* ip4, float* ipL, cudaStream_t s);
 cudaError_t launch_layout(const float2* c, const float* m, int ones, float4* volX, float4* volY,
                           int nx, int ny, int nz, cudaStream_t s);
+int forward_blocks_per_sm();
 cudaError_t launch_forward(int mode, const Geo& G, const Spec& S, const FwdArgs& A, int n_blocks,
                            cudaStream_t s);
 cudaError_t launch_backward(int mode, int slab, const Geo& G, const BwdArgs& A, cudaStream_t s);

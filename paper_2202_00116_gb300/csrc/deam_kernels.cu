@@ -12,6 +12,8 @@
 // bound by gather/FMA issue, the rest by HBM.
 #include <math.h>
 
+#include <algorithm>
+
 #include "deam_epilogue.cuh"
 #include "deam_internal.h"
 
@@ -742,6 +744,17 @@ cudaError_t launch_layout(const float2* c, const float* m, int ones, float4* vol
         else layout_kernel<0><<<g, 256, 0, s>>>(c, m, vol, axis, nx, ny, nz);
     }
     return cudaGetLastError();
+}
+
+// Resident blocks per SM of the heaviest single-scan forward kernel: the
+// persistent forward grid is this many blocks per SM (one wave; a larger grid
+// of equal-work blocks leaves a partial second wave).
+int forward_blocks_per_sm() {
+    int a = 0, b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, fwd_kernel<FWD_DEAM>, kFwdThreads, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fwd_kernel<FWD_DEAM_F32>, kFwdThreads, 0) != cudaSuccess)
+        return 4;
+    return std::max(1, std::min(a, b));
 }
 
 cudaError_t launch_forward(int mode, const Geo& G, const Spec& S, const FwdArgs& A, int n_blocks, cudaStream_t s) {
