@@ -1,4 +1,4 @@
-"""ctypes binding of the FP64 CPU oracle (``deam_oracle.c``).
+"""ctypes binding of the FP64 CPU oracle (``deam_oracle.c``, ``mar_init_oracle.c``).
 
 TEST INFRASTRUCTURE ONLY: the oracle is what the CUDA path is checked against.
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
@@ -17,7 +17,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "deam_oracle.c")
+_SRCS = [os.path.join(_HERE, f) for f in ("deam_oracle.c", "mar_init_oracle.c", "or_types.h")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -41,6 +41,12 @@ class Model(C.Structure):
                 ("bowtie", C.POINTER(C.c_double))]
 
 
+class MarParams(C.Structure):
+    _fields_ = [("calib", C.c_double * 4), ("t_air", C.c_double), ("t_bone", C.c_double),
+                ("soft_value", C.c_double), ("count_floor", C.c_double), ("eps", C.c_double),
+                ("prior_spectrum", C.c_int)]
+
+
 class Tap(C.Structure):
     _fields_ = [("idx", C.c_long), ("w", C.c_double)]
 
@@ -49,12 +55,12 @@ def build(force: bool = False) -> str:
     """Compile the oracle with gcc (OpenMP, no FMA contraction, no fast-math)."""
     with _lock:
         if (not force and os.path.exists(_LIB)
-                and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+                and os.path.getmtime(_LIB) >= max(os.path.getmtime(f) for f in _SRCS)):
             return _LIB
         os.makedirs(_BUILD, exist_ok=True)
         tmp = _LIB + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-               "-o", tmp, _SRC, "-lm"]
+               "-o", tmp] + [f for f in _SRCS if f.endswith(".c")] + ["-lm"]
         subprocess.check_call(cmd)
         os.replace(tmp, _LIB)
         return _LIB
@@ -87,6 +93,14 @@ def lib():
             "or_phi": (d, [d, d]),
             "or_penalty": (d, [G, pd, d, d]),
             "or_iterate_reg": (l, [G, M, pd, pd, pu8, i, pd, pd, d, i, d, d]),
+            "or_log_sinogram": (None, [G, M, pd, d, pd]),
+            "or_complete_trace": (None, [G, pd, pd, pu8, i, d, pd]),
+            "or_ramp_filter": (None, [G, pd, pd]),
+            "or_fbp_backproject": (None, [G, pd, pd]),
+            "or_fbp": (None, [G, pd, pd]),
+            "or_prior": (None, [l, pd, d, d, d, pd]),
+            "or_decompose": (None, [l, pd, pd, pd, pd]),
+            "or_mar_init": (None, [G, M, pd, pu8, P(MarParams), pd, pd, pd, pd, pd]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -262,6 +276,74 @@ class Oracle:
         out = np.zeros(self.img_shape)
         self.L.or_gradient(C.byref(self.g), C.byref(self.m), _p(c), _p(d), _p(mask, C.c_uint8), _p(out))
         return out
+
+    # ---- MAR initialisation (Sec. 2.2, Eq. 4) ----
+    def log_sinogram(self, d, floor_counts=1.0):
+        d = _f64(_np(d)).reshape((2,) + self.ray_shape)
+        out = np.zeros((2,) + self.ray_shape)
+        self.L.or_log_sinogram(C.byref(self.g), C.byref(self.m), _p(d), float(floor_counts), _p(out))
+        return out
+
+    def complete_trace(self, p, mask, bit, prior_proj=None, eps=1e-3):
+        """NMAR (prior_proj given) or LI (None) completion of one sinogram [V,R,K]
+        across the rays with mask bit `bit` set (mask in the oracle's bit encoding)."""
+        p = _f64(_np(p)).reshape(self.ray_shape)
+        mk = np.ascontiguousarray(_np(mask).reshape(self.ray_shape), dtype=np.uint8)
+        pr = None if prior_proj is None else _f64(_np(prior_proj)).reshape(self.ray_shape)
+        out = np.zeros(self.ray_shape)
+        self.L.or_complete_trace(C.byref(self.g), _p(p), _p(pr) if pr is not None else C.POINTER(C.c_double)(),
+                                 _p(mk, C.c_uint8), int(bit), float(eps), _p(out))
+        return out
+
+    def ramp_filter(self, p):
+        p = _f64(_np(p)).reshape(self.ray_shape)
+        out = np.zeros(self.ray_shape)
+        self.L.or_ramp_filter(C.byref(self.g), _p(p), _p(out))
+        return out
+
+    def fbp_backproject(self, q):
+        q = _f64(_np(q)).reshape(self.ray_shape)
+        out = np.zeros(self.img_shape[:3])
+        self.L.or_fbp_backproject(C.byref(self.g), _p(q), _p(out))
+        return out
+
+    def fbp(self, p):
+        p = _f64(_np(p)).reshape(self.ray_shape)
+        out = np.zeros(self.img_shape[:3])
+        self.L.or_fbp(C.byref(self.g), _p(p), _p(out))
+        return out
+
+    def mar_init(self, d, mask, calib, t_air, t_bone, soft_value, count_floor=1.0, eps=1e-3,
+                 prior_spectrum=1, prior=None):
+        """(c [nz,ny,nx,2], prior, mu_L, mu_H) of the MAR initialisation; `prior`
+        (optional) replaces the thresholded prior image."""
+        d, mk = self._dm(d, mask)
+        P = MarParams((C.c_double * 4)(*[float(x) for x in np.asarray(calib).reshape(4)]), float(t_air),
+                      float(t_bone), float(soft_value), float(count_floor), float(eps), int(prior_spectrum))
+        shp = self.img_shape[:3]
+        pin = None if prior is None else _f64(_np(prior)).reshape(shp)
+        c = np.zeros(self.img_shape)
+        po, mL, mH = np.zeros(shp), np.zeros(shp), np.zeros(shp)
+        self.L.or_mar_init(C.byref(self.g), C.byref(self.m), _p(d), _p(mk, C.c_uint8), C.byref(P),
+                           _p(pin) if pin is not None else C.POINTER(C.c_double)(), _p(c), _p(po), _p(mL), _p(mH))
+        return c, po, mL, mH
+
+
+def prior_image(f, t_air, t_bone, soft_value):
+    """Thresholded prior of a single-energy FBP image f (Sec. 2.2)."""
+    f = _f64(_np(f))
+    out = np.zeros_like(f)
+    lib().or_prior(f.size, _p(f), float(t_air), float(t_bone), float(soft_value), _p(out))
+    return out
+
+
+def decompose(mu_L, mu_H, calib):
+    """Eq. (4) with constant calibrated weights calib = (mu~_1L, mu~_2L, mu~_1H, mu~_2H)."""
+    mL, mH = _f64(_np(mu_L)), _f64(_np(mu_H))
+    cal = np.ascontiguousarray(np.asarray(calib, dtype=np.float64).reshape(4))
+    out = np.zeros(mL.shape + (2,))
+    lib().or_decompose(mL.size, _p(mL), _p(mH), _p(cal), _p(out))
+    return out
 
 
 def phi(u, delta):

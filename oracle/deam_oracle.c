@@ -47,28 +47,7 @@
 #define M_PI 3.14159265358979323846
 #endif
 
-typedef struct {
-    int kind, nx, ny, nz;
-    double dx, dy, dz, cx, cy, cz, sid, sdd;
-    int n_views, views_per_rotation;
-    double start_angle, feed, z_start;
-    int n_rows;
-    double row_pitch;
-    int n_channels;
-    double channel_pitch, channel_offset, row_offset;
-} or_geometry;
-
-typedef struct {
-    int n_e;
-    const double *I0;     /* [2][n_e] */
-    const double *mu;     /* [2][n_e] */
-    const double *bowtie; /* [n_channels] or NULL (== 1) */
-} or_model;
-
-typedef struct {
-    long idx;  /* voxel index iz*ny*nx + iy*nx + ix */
-    double w;  /* h(x, y) in mm */
-} or_tap;
+#include "or_types.h"
 
 int or_max_taps(const or_geometry *g) { return 4 * (g->nx > g->ny ? g->nx : g->ny); }
 
