@@ -190,6 +190,59 @@ int deam_gradient(deam_ctx *ctx, const float *c, float *grad, double *F, void *s
  * deam_set_data.  Deterministic. */
 int deam_backprojected_sums(deam_ctx *ctx, const float *c, float *sums, double *F, double *Z, void *stream);
 
+/* ---- MAR initialisation (Sec. 2.2 and Eq. 4) ---------------------------------
+ * The starting image c^0 of MAR-DEAM: the measured sinograms of both spectra
+ * are completed across their metal traces by normalised metal-artifact
+ * reduction (NMAR: divide by the forward projection of a prior image,
+ * interpolate linearly along the channels, multiply back), reconstructed by
+ * filtered backprojection, and split into the basis components by the
+ * image-domain decomposition of Eq. (4).  The prior thresholds a
+ * single-energy FBP image (Sec. 2.2: "prior image by thresholding").
+ * FBP: equiangular fan-beam filtered backprojection on the curved detector
+ * (pre-weight SID cos(gamma), the discrete equiangular ramp kernel), extended
+ * to the helix FDK-style (cone pre-weight SDD / sqrt(SDD^2 + w^2); each voxel
+ * takes the one rotation of views centred on the view whose source z equals
+ * its own, rows interpolated at w = (z - z_s) SDD / L and clamped to the end
+ * rows; channels outside the detector contribute nothing).  All need
+ * deam_set_data; trace completion needs the metal mask.  Work is enqueued on
+ * `stream`; scratch is allocated per call (these run once per scan). */
+typedef struct deam_mar_params {
+    double calib[4];       /* mu~_1L, mu~_2L, mu~_1H, mu~_2H of Eq. (4): FBP value (1/mm) of unit c_i
+                              in the spectrum-j image; the 2x2 matrix must be invertible */
+    double t_air;          /* prior: FBP values below -> 0 (1/mm) */
+    double t_bone;         /* prior: values at or above are kept (1/mm) */
+    double soft_value;     /* prior: value of voxels in [t_air, t_bone) (1/mm) */
+    double count_floor;    /* counts: d~ is floored here before the log (> 0; 1 is typical) */
+    double eps;            /* NMAR: the prior projection is floored here before dividing (> 0) */
+    int prior_spectrum;    /* single-energy image of the prior: 0 = L, 1 = H */
+    int reserved[7];       /* zero */
+} deam_mar_params;
+
+/* Line-integral sinograms p_j(y) = ln(I0_j(y) / max(d~_j(y), count_floor)),
+ * I0_j(y) = sum_E I0_j(E) bowtie(k).  p: device float32 [2][V][R][K]. */
+int deam_log_sinogram(deam_ctx *ctx, double count_floor, float *p, void *stream);
+
+/* Trace completion of one sinogram p (device float32 [V][R][K]) into out (same
+ * shape; may equal p) over the rays whose mask bit `spectrum` (0 = L, 1 = H) is
+ * set: linear interpolation along the channels of each (view, row) between the
+ * nearest rays off the trace (constant beyond the row's ends).  With prior_proj
+ * (device float32 [V][R][K], the prior image's projection) the interpolated
+ * quantity is p / max(prior_proj, eps), multiplied back afterwards (NMAR);
+ * with NULL it is p itself.  Rays off the trace are copied unchanged. */
+int deam_complete_trace(deam_ctx *ctx, const float *p, const float *prior_proj, int spectrum, double eps,
+                        float *out, void *stream);
+
+/* FBP images img[i] (device float32 [n][nz][ny][nx], 1/mm) of n = 1 or 2
+ * line-integral sinograms p[i] (device float32 [n][V][R][K]). */
+int deam_fbp(deam_ctx *ctx, const float *p, int n, float *img, void *stream);
+
+/* The whole initialisation into c (device float32 [nz][ny][nx][2]).  prior_in
+ * (nullable, device float32 [nz][ny][nx]) replaces the thresholded prior;
+ * prior_out (nullable, same shape) receives the prior used; mu_out (nullable,
+ * device float32 [2][nz][ny][nx]) the two NMAR-corrected FBP images. */
+int deam_mar_init(deam_ctx *ctx, const deam_mar_params *params, const float *prior_in, float *c, float *prior_out,
+                  float *mu_out, void *stream);
+
 /* Linear images of the basis components (Sec. 3): out[e] = a_e c_1 + b_e c_2 for
  * n coefficient pairs coef[2e] = a_e, coef[2e+1] = b_e (host, 1 <= n <= 256).
  * With (a_e, b_e) = (mu_1(E_e), mu_2(E_e)) these are virtual monoenergetic

@@ -52,6 +52,12 @@ class deam_options(C.Structure):
                 ("reserved", C.c_int * 6)]
 
 
+class deam_mar_params(C.Structure):
+    _fields_ = [("calib", C.c_double * 4), ("t_air", C.c_double), ("t_bone", C.c_double),
+                ("soft_value", C.c_double), ("count_floor", C.c_double), ("eps", C.c_double),
+                ("prior_spectrum", C.c_int), ("reserved", C.c_int * 7)]
+
+
 class DeamError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"deam error {code}: {msg}")
@@ -62,7 +68,8 @@ _lib = None
 EXPORTS = ["deam_init", "deam_set_data", "deam_set_metal_mask", "deam_get_metal_mask", "deam_forward",
            "deam_backproject", "deam_ray_terms", "deam_iterate", "deam_objective", "deam_info",
            "deam_gradient", "deam_backprojected_sums", "deam_penalty", "deam_basis_images", "deam_count_samples",
-           "deam_profile", "deam_kernel_times", "deam_batch_create",
+           "deam_profile", "deam_kernel_times", "deam_log_sinogram", "deam_complete_trace", "deam_fbp",
+           "deam_mar_init", "deam_batch_create",
            "deam_batch_iterate", "deam_batch_info", "deam_batch_destroy", "deam_objective_noalloc",
            "deam_destroy", "deam_last_error"]
 
@@ -94,6 +101,10 @@ def lib():
             "deam_count_samples": [vp, C.POINTER(C.c_longlong), vp],
             "deam_profile": [vp, i],
             "deam_kernel_times": [vp, pd, C.POINTER(C.c_longlong), i],
+            "deam_log_sinogram": [vp, C.c_double, vp, vp],
+            "deam_complete_trace": [vp, vp, vp, i, C.c_double, vp, vp],
+            "deam_fbp": [vp, vp, i, vp, vp],
+            "deam_mar_init": [vp, C.POINTER(deam_mar_params), vp, vp, vp, vp, vp],
             "deam_objective_noalloc": [C.POINTER(deam_geometry), C.POINTER(deam_spectra), C.POINTER(deam_basis),
                                        vp, vp, vp, vp, vp],
             "deam_batch_create": [C.POINTER(vp), i, i, C.POINTER(vp)],
@@ -291,6 +302,54 @@ class Deam:
                                   self._stream()))
         return R.value
 
+    # -- MAR initialisation (Sec. 2.2, Eq. 4) --
+    def log_sinogram(self, count_floor=1.0):
+        """Line-integral sinograms p [2, V, R, K] = ln(I0_j / max(d~_j, count_floor))."""
+        torch = self.torch
+        p = torch.empty((2,) + self.ray_shape, dtype=torch.float32, device=self.device)
+        _check(lib().deam_log_sinogram(self._h, float(count_floor), C.c_void_p(p.data_ptr()), self._stream()))
+        return p
+
+    def complete_trace(self, p, spectrum, prior_proj=None, eps=1e-3, out=None):
+        """Trace completion of one sinogram [V, R, K] over spectrum's trace: NMAR
+        with the prior's projection, else linear interpolation."""
+        torch = self.torch
+        if out is None:
+            out = torch.empty(self.ray_shape, dtype=torch.float32, device=self.device)
+        pp = C.c_void_p(None) if prior_proj is None else self._arg(prior_proj, self.ray_shape, torch.float32)
+        _check(lib().deam_complete_trace(self._h, self._arg(p, self.ray_shape, torch.float32), pp, int(spectrum),
+                                         float(eps), self._arg(out, self.ray_shape, torch.float32), self._stream()))
+        return out
+
+    def fbp(self, p):
+        """FBP image(s) [n, nz, ny, nx] (1/mm) of line-integral sinogram(s) [n, V, R, K]
+        or [V, R, K] (n = 1, 2)."""
+        torch = self.torch
+        single = p.dim() == 3
+        pp = p.unsqueeze(0) if single else p
+        n = pp.shape[0]
+        img = torch.empty((n,) + self.img_shape[:3], dtype=torch.float32, device=self.device)
+        _check(lib().deam_fbp(self._h, self._arg(pp.contiguous(), (n,) + self.ray_shape, torch.float32), n,
+                              C.c_void_p(img.data_ptr()), self._stream()))
+        return img[0] if single else img
+
+    def mar_init(self, calib, t_air, t_bone, soft_value, count_floor=1.0, eps=1e-3, prior_spectrum=1,
+                 prior=None):
+        """(c^0 [nz, ny, nx, 2], prior [nz, ny, nx], mu [2, nz, ny, nx]): NMAR-corrected
+        FBP images of both spectra split by Eq. (4) with calib = (mu~_1L, mu~_2L,
+        mu~_1H, mu~_2H); `prior` replaces the thresholded prior image."""
+        torch = self.torch
+        P = deam_mar_params((C.c_double * 4)(*[float(x) for x in np.asarray(calib, dtype=np.float64).reshape(4)]),
+                            float(t_air), float(t_bone), float(soft_value), float(count_floor), float(eps),
+                            int(prior_spectrum))
+        c = torch.empty(self.img_shape, dtype=torch.float32, device=self.device)
+        pr = torch.empty(self.img_shape[:3], dtype=torch.float32, device=self.device)
+        mu = torch.empty((2,) + self.img_shape[:3], dtype=torch.float32, device=self.device)
+        pin = C.c_void_p(None) if prior is None else self._arg(prior, self.img_shape[:3], torch.float32)
+        _check(lib().deam_mar_init(self._h, C.byref(P), pin, C.c_void_p(c.data_ptr()), C.c_void_p(pr.data_ptr()),
+                                   C.c_void_p(mu.data_ptr()), self._stream()))
+        return c, pr, mu
+
     def basis_images(self, c, coef):
         """out[e] = coef[e, 0] c_1 + coef[e, 1] c_2, float32 [n, nz, ny, nx]."""
         torch = self.torch
@@ -354,6 +413,24 @@ class Deam:
 
 def from_case(case, **kw) -> Deam:
     return Deam(case.geo, case.I0, case.mu, bowtie=case.bowtie, energies=case.energies, **kw)
+
+
+def calibrate_decomposition(scans, roi):
+    """Calibrated weights (mu~_1L, mu~_2L, mu~_1H, mu~_2H) of Eq. (4) from
+    calibration scans: `scans` is a list of (deam, (c1, c2)) pairs, each a
+    context holding the counts of a calibration phantom whose ROI (boolean
+    [nz, ny, nx] tensor) has basis densities (c1, c2).  Each scan's two FBP
+    images are averaged over the ROI and mu_j = mu~_1j c1 + mu~_2j c2 is solved
+    by least squares over the scans (at least two with independent (c1, c2))."""
+    A, b = [], []
+    for dm, cc in scans:
+        mu = dm.fbp(dm.log_sinogram()).cpu().double().numpy()
+        r = np.asarray(roi.cpu() if hasattr(roi, "cpu") else roi, dtype=bool)
+        b.append([float(mu[j][r].mean()) for j in range(2)])
+        A.append([float(cc[0]), float(cc[1])])
+    A, b = np.asarray(A), np.asarray(b)
+    sol = np.linalg.lstsq(A, b, rcond=None)[0]   # [[m1L, m1H], [m2L, m2H]]
+    return np.array([sol[0, 0], sol[1, 0], sol[0, 1], sol[1, 1]])
 
 
 def objective_noalloc(geo, I0, mu, c, d, mask, F, bowtie=None):

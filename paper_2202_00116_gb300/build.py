@@ -12,7 +12,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdeam.so")
-SOURCES = ["deam_kernels.cu", "deam_api.cu", "deam_batch.cu", "deam_noalloc.cu"]
+SOURCES = ["deam_kernels.cu", "deam_api.cu", "deam_batch.cu", "deam_noalloc.cu", "deam_mar.cu"]
 HEADERS = ["deam_internal.h", "deam_epilogue.cuh", "deam_ctx.h", os.path.join("..", "..", "include", "deam.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]

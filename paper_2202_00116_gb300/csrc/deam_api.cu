@@ -279,6 +279,8 @@ int deam_init(const deam_geometry* geom, const deam_spectra* spectra, const deam
     double mumax = 0.0;
     for (int e = 0; e < nE; ++e) {
         const double il = spectra->I0[e], ih = spectra->I0[nE + e];
+        ctx->i0tot[0] += il;
+        ctx->i0tot[1] += ih;
         const double m1 = basis->mu[e], m2 = basis->mu[nE + e];
         S.mu1l2[e] = (float)(m1 * log2e);
         S.mu2l2[e] = (float)(m2 * log2e);

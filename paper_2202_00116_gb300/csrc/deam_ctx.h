@@ -17,6 +17,7 @@ struct deam_ctx {
     int clamp = 0;
     double lambda = 0.0, delta = 1.0;  // penalty of Eqs. (6)-(7)
     int fwd_mode = deam::FWD_DEAM;     // FWD_DEAM_F32 for the plain-FP32 variant
+    double i0tot[2] = {0.0, 0.0};      // sum_E I0_j(E) (MAR initialisation's log sinograms)
     bool has_data = false, mask_set = false, failed = false;
     long long nrays = 0, nvox = 0, skipped_last = 0;
     int n_fwd_blocks = 0, n_slabs = 0, slab = 16;
