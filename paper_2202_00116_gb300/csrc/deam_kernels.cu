@@ -346,7 +346,10 @@ __device__ __forceinline__ void bwd_tile(const Geo& G, const BwdArgs& A, float4*
             int r0 = 0, r1 = G.R - 1;
             if (G.R > 1) {
                 // fz(r) ~= sigma_z + t_p (omega0 + r domega): rows whose sample can
-                // land in [z0 - 1, z0 + SLAB) (one row of margin each side)
+                // land in [z0 - 1, z0 + SLAB).  The approximate row model and the
+                // fast reciprocal are within ~1e-6 rows of the exact samples; a
+                // 0.02-row margin keeps every contributing row, and the exact
+                // per-row slot test below decides.
                 const float tp = fmaf(pf, ip.kappa, ip.tau0);
                 const float slope = tp * G.domega;
                 if (fabsf(slope) > 1e-20f) {
@@ -355,8 +358,8 @@ __device__ __forceinline__ void bwd_tile(const Geo& G, const BwdArgs& A, float4*
                     const float ra = (zlo - base) * inv, rb = (zhi - base) * inv;
                     const float lo = fminf(fmaxf(fminf(ra, rb), -4.f), (float)G.R + 4.f);
                     const float hi = fminf(fmaxf(fmaxf(ra, rb), -4.f), (float)G.R + 4.f);
-                    r0 = max(0, (int)floorf(lo) - 1);
-                    r1 = min(G.R - 1, (int)ceilf(hi) + 1);
+                    r0 = max(0, (int)floorf(lo - 0.02f));
+                    r1 = min(G.R - 1, (int)ceilf(hi + 0.02f));
                 }
             }
             const float Lq = ip.Lxy * wq;
