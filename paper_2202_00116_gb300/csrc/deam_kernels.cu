@@ -316,7 +316,10 @@ __device__ __forceinline__ void bwd_tile(const Geo& G, const BwdArgs& A, float4*
         const float sz = __ldg(&G.view_z[v]);
         float dist;
         const float uc = channel_coord(G, vw, fix, fiy, &dist);
-        const float hw = __fdividef(G.vox_reach_mm, fmaxf(dist - G.vox_reach_mm, 1.f)) * G.inv_dgamma + 1.f;
+        // a ray can tap the column only if it passes within one voxel edge of
+        // its centre: |gamma - gamma_c| < asin(edge / dist) < reach / (dist - reach);
+        // 0.05 channel of margin covers the FP32 channel coordinate
+        const float hw = __fdividef(G.vox_reach_mm, fmaxf(dist - G.vox_reach_mm, 1.f)) * G.inv_dgamma + 0.05f;
         const int k0 = max(0, (int)ceilf(fmaxf(uc - hw, -1.f)));
         const int k1 = min(G.K - 1, (int)floorf(fminf(uc + hw, (float)G.K)));
         const long long vbase = (long long)v * G.K;
