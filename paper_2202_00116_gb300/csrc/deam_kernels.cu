@@ -374,7 +374,7 @@ __device__ __forceinline__ void bwd_tile(const Geo& G, const BwdArgs& A, float4*
             int ls = -1000;
             // ray data [V][R][K]: a warp's columns read neighbouring channels of a row
             const long long pb = vbase * G.R + k;
-#pragma unroll 2
+#pragma unroll 4
             for (int r = r0; r <= r1; ++r) {
                 float4 Pv;
                 if (MODE == BWD_ADJOINT) {
