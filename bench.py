@@ -41,7 +41,7 @@ FP32_LANES_PER_SM = 128
 # captures of the same kernels on the one-rotation cut of this scan (6.48e9
 # samples per launch); traffic grows with the views, so it is scaled by the
 # sample count of the measured launch.  Valid for the kernel builds captured.
-DRAM_BYTES_PER_SAMPLE = {"bwd_kernel<1,16>": 3.178e9 / 6.484e9}
+DRAM_BYTES_PER_SAMPLE = {"bwd_kernel<1,16>": 3.135e9 / 6.484e9, "fwd_kernel<FWD_DEAM>": 11.316e9 / 6.484e9}
 
 
 def _peaks():
