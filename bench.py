@@ -42,6 +42,10 @@ FP32_LANES_PER_SM = 128
 # samples per launch); traffic grows with the views, so it is scaled by the
 # sample count of the measured launch.  Valid for the kernel builds captured.
 DRAM_BYTES_PER_SAMPLE = {"bwd_kernel<1,16>": 3.135e9 / 6.484e9, "fwd_kernel<FWD_DEAM>": 11.316e9 / 6.484e9}
+# L1/TEX (load/store + shared memory data path) utilisation of the same kernels
+# in those captures: the unit that actually bounds them (no step is a dense
+# contraction and DRAM runs at 1-10 % of peak).
+L1_BUSY = {"bwd_kernel<1,16>": 0.955, "fwd_kernel<FWD_DEAM>": 0.739}
 
 
 def _peaks():
@@ -319,6 +323,7 @@ def finish_line(args, world, rank, pg, gpu, case, d, mask, c0, samples, ms, valu
                 "traffic_note": "ncu dram__bytes_read+write per launch, scaled by Joseph samples from the "
                                 "one-rotation capture (profiles/)",
                 "ms_per_launch": avg[dom],
+                "l1tex_busy_ncu": L1_BUSY.get(kname),
                 "hbm_compulsory_GBps": None}
     nvox, nrays = geo.n_voxels, geo.n_rays
     comp_bytes = {"forward": 16 * nvox + 8 * nrays + nrays + 16 * nrays,

@@ -103,8 +103,10 @@ __device__ __forceinline__ double fwd_ray(const Geo& G, const Spec& S, const Fwd
     const float L = __fmul_rn(ip.Lxy, rw.y);
     const float l1 = s1 * L, l2 = s2 * L;
 
+    // outputs are streamed (evict-first) so that they do not push the volume
+    // layouts out of L2
     if (MODE == FWD_LINE) {
-        A.l_out[y] = make_float2(l1, l2);
+        __stcs(&A.l_out[y], make_float2(l1, l2));
     } else if (MODE == FWD_MASK) {
         A.mask_out[y] = (uint8_t)(l1 >= A.threshold ? 3 : 0);  // one operator: both spectra
     } else if (MODE == FWD_MAX) {
@@ -115,9 +117,9 @@ __device__ __forceinline__ double fwd_ray(const Geo& G, const Spec& S, const Fwd
         float gl, gh, a, b, c, d;
         spectral_sums<false>(S, l1, l2, gl, gh, a, b, c, d);
         const float bk = A.bowtie ? __ldg(&A.bowtie[k]) : 1.f;
-        if (A.l_out) A.l_out[y] = make_float2(l1, l2);
-        A.g_out[y] = gl * bk;
-        A.g_out[nrays + y] = gh * bk;
+        if (A.l_out) __stcs(&A.l_out[y], make_float2(l1, l2));
+        __stcs(&A.g_out[y], gl * bk);
+        __stcs(&A.g_out[nrays + y], gh * bk);
     } else {  // FWD_DEAM, FWD_DEAM_F32
         float gl, gh, s1l, s2l, s1h, s2h;
         spectral_sums<true, MODE == FWD_DEAM>(S, l1, l2, gl, gh, s1l, s2l, s1h, s2h);
