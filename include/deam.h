@@ -233,7 +233,8 @@ int deam_complete_trace(deam_ctx *ctx, const float *p, const float *prior_proj, 
                         float *out, void *stream);
 
 /* FBP images img[i] (device float32 [n][nz][ny][nx], 1/mm) of n = 1 or 2
- * line-integral sinograms p[i] (device float32 [n][V][R][K]). */
+ * line-integral sinograms p[i] (device float32 [n][V][R][K]).  FBP (here and in
+ * deam_mar_init) supports 2 to 3072 channels; more return DEAM_ERR_ARG. */
 int deam_fbp(deam_ctx *ctx, const float *p, int n, float *img, void *stream);
 
 /* The whole initialisation into c (device float32 [nz][ny][nx][2]).  prior_in

@@ -58,6 +58,10 @@ struct FbpGeo {
     float dbeta;                   // 2 pi / views per rotation
 };
 
+// The ramp filter keeps a zero-padded row (3K floats) and the kernel (K floats)
+// in shared memory: 16 K bytes within the default 48 KB per block.
+constexpr int kMaxFbpChannels = 3072;
+
 int grid_for(long long n, int threads) {
     return (int)std::max<long long>(1, std::min<long long>((n + threads - 1) / threads, 152LL * 32));
 }
@@ -385,7 +389,8 @@ int deam_fbp(deam_ctx* ctx, const float* p, int n, float* img, void* stream) {
     CHECK_READY(ctx);
     if (n != 1 && n != 2) return fail(DEAM_ERR_ARG, "n must be 1 or 2");
     if (!p || !img || !is_dev(p) || !is_dev(img)) return fail(DEAM_ERR_ARG, "p and img must be device pointers");
-    if (ctx->geo.n_channels < 2) return fail(DEAM_ERR_ARG, "FBP needs at least 2 channels");
+    if (ctx->geo.n_channels < 2 || ctx->geo.n_channels > kMaxFbpChannels)
+        return fail(DEAM_ERR_ARG, "FBP needs 2 to 3072 channels (the ramp filter stages a row in shared memory)");
     DevGuard dg(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     float* q = nullptr;
@@ -409,7 +414,8 @@ int deam_mar_init(deam_ctx* ctx, const deam_mar_params* P, const float* prior_in
     if (!(isfinite(P->count_floor) && P->count_floor > 0.0)) return fail(DEAM_ERR_ARG, "count_floor must be > 0");
     if (!(isfinite(P->eps) && P->eps > 0.0)) return fail(DEAM_ERR_ARG, "eps must be > 0");
     if (P->prior_spectrum != 0 && P->prior_spectrum != 1) return fail(DEAM_ERR_ARG, "prior_spectrum must be 0 or 1");
-    if (ctx->geo.n_channels < 2) return fail(DEAM_ERR_ARG, "FBP needs at least 2 channels");
+    if (ctx->geo.n_channels < 2 || ctx->geo.n_channels > kMaxFbpChannels)
+        return fail(DEAM_ERR_ARG, "FBP needs 2 to 3072 channels (the ramp filter stages a row in shared memory)");
     DevGuard dg(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     const long long nr = ctx->nrays, nv = ctx->nvox;
