@@ -70,3 +70,37 @@ def test_null_context_calls_fail_cleanly(libdeam):
     assert L.deam_iterate(None, None, 1, None, None) == libdeam.DEAM_ERR_ARG
     assert L.deam_destroy(None) == libdeam.DEAM_OK
     assert b"null" in L.deam_last_error()
+
+
+def test_every_context_entry_point_rejects_a_null_context(libdeam):
+    # host-side argument checks run before any device call, so they are
+    # exercised here without a GPU
+    L = libdeam.lib()
+    P = libdeam.deam_mar_params()
+    calls = [
+        lambda: L.deam_set_data(None, None, None),
+        lambda: L.deam_forward(None, None, None, None, None),
+        lambda: L.deam_backproject(None, None, None, None),
+        lambda: L.deam_ray_terms(None, None, None, None, None),
+        lambda: L.deam_objective(None, None, None, None),
+        lambda: L.deam_gradient(None, None, None, None, None),
+        lambda: L.deam_backprojected_sums(None, None, None, None, None, None),
+        lambda: L.deam_penalty(None, None, None, None),
+        lambda: L.deam_log_sinogram(None, 1.0, None, None),
+        lambda: L.deam_complete_trace(None, None, None, 0, 1e-3, None, None),
+        lambda: L.deam_fbp(None, None, 1, None, None),
+        lambda: L.deam_mar_init(None, C.byref(P), None, None, None, None, None),
+    ]
+    for call in calls:
+        assert call() == libdeam.DEAM_ERR_ARG
+        assert b"null" in L.deam_last_error().lower()
+
+
+def test_binding_fails_loudly_without_the_library(libdeam, monkeypatch, tmp_path):
+    # no CPU fallback: with the compiled library missing, the binding raises
+    monkeypatch.setattr(libdeam, "LIB_PATH", str(tmp_path / "missing" / "libdeam.so"))
+    monkeypatch.setattr(libdeam, "_lib", None)
+    import synth
+    case = synth.make_case("t2d")
+    with pytest.raises(RuntimeError, match="missing"):
+        libdeam.Deam(case.geo, case.I0, case.mu)
