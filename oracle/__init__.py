@@ -98,6 +98,7 @@ def lib():
             "or_ramp_filter": (None, [G, pd, pd]),
             "or_fbp_backproject": (None, [G, pd, pd]),
             "or_fbp": (None, [G, pd, pd]),
+            "or_fbp_backproject_at": (None, [G, pd, pi64, l, pd]),
             "or_prior": (None, [l, pd, d, d, d, pd]),
             "or_decompose": (None, [l, pd, pd, pd, pd]),
             "or_mar_init": (None, [G, M, pd, pu8, P(MarParams), pd, pd, pd, pd, pd]),
@@ -305,6 +306,15 @@ class Oracle:
         q = _f64(_np(q)).reshape(self.ray_shape)
         out = np.zeros(self.img_shape[:3])
         self.L.or_fbp_backproject(C.byref(self.g), _p(q), _p(out))
+        return out
+
+    def fbp_backproject_at(self, q, voxels):
+        """FBP backprojection of the filtered sinogram q [V,R,K] at the listed
+        voxel indices (iz*ny*nx + iy*nx + ix) only."""
+        q = _f64(_np(q)).reshape(self.ray_shape)
+        vox = np.ascontiguousarray(_np(voxels), dtype=np.int64)
+        out = np.zeros(vox.size)
+        self.L.or_fbp_backproject_at(C.byref(self.g), _p(q), _p(vox, C.c_int64), vox.size, _p(out))
         return out
 
     def fbp(self, p):

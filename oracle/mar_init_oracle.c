@@ -159,57 +159,67 @@ static void view_window(const or_geometry *g, double Z, long *v0, long *v1) {
     *v1 = b;
 }
 
-/* FBP backprojection of the filtered sinogram q [V][R][K] into img [nz][ny][nx]. */
-void or_fbp_backproject(const or_geometry *g, const double *q, double *img) {
+/* FBP backprojection value at one voxel (index iz*ny*nx + iy*nx + ix). */
+static double fbp_voxel(const or_geometry *g, const double *q, long vi) {
     const int K = g->n_channels, R = g->n_rows;
     const long N = g->views_per_rotation;
     const double X0 = g->cx - (g->nx - 1) / 2.0 * g->dx;
     const double Y0 = g->cy - (g->ny - 1) / 2.0 * g->dy;
     const double Z0 = g->cz - (g->nz - 1) / 2.0 * g->dz;
-    const long nvox = (long)g->nx * g->ny * g->nz;
     const double dbeta = 2.0 * M_PI / (double)N;
-#pragma omp parallel for schedule(dynamic, 256)
-    for (long vi = 0; vi < nvox; vi++) {
-        int ix = (int)(vi % g->nx), iy = (int)((vi / g->nx) % g->ny), iz = (int)(vi / ((long)g->nx * g->ny));
-        double X = X0 + ix * g->dx, Y = Y0 + iy * g->dy, Z = Z0 + iz * g->dz;
-        long v0, v1;
-        view_window(g, Z, &v0, &v1);
-        double acc = 0.0;
-        for (long v = v0; v < v1; v++) {
-            double beta = g->start_angle + 2.0 * M_PI * (double)v / (double)N;
-            double sx = g->sid * cos(beta), sy = g->sid * sin(beta);
-            double sz = g->z_start + g->feed * (double)v / (double)N;
-            double ddx = X - sx, ddy = Y - sy;
-            double L2 = ddx * ddx + ddy * ddy, L = sqrt(L2);
-            /* the ray of fan angle gamma points along beta + gamma + pi */
-            double gam = atan2(ddy, ddx) - beta - M_PI;
-            gam = gam - 2.0 * M_PI * floor((gam + M_PI) / (2.0 * M_PI));
-            double kf = gam / g->channel_pitch + (K - 1) / 2.0 - g->channel_offset;
-            if (!(kf >= 0.0 && kf <= K - 1)) continue;
-            double rf = 0.0;
-            if (R > 1) {
-                double w = (Z - sz) * g->sdd / L;
-                rf = w / g->row_pitch + (R - 1) / 2.0 - g->row_offset;
-                if (rf < 0.0) rf = 0.0;
-                if (rf > R - 1) rf = R - 1;
-            }
-            int k0 = (int)floor(kf), r0 = (int)floor(rf);
-            if (k0 > K - 2) k0 = K - 2 < 0 ? 0 : K - 2;
-            if (r0 > R - 2) r0 = R - 2 < 0 ? 0 : R - 2;
-            double ak = kf - k0, ar = rf - r0;
-            const double *qv = q + (long)v * R * K;
-            double val;
-            if (R > 1) {
-                double lo = (1.0 - ak) * qv[(long)r0 * K + k0] + ak * qv[(long)r0 * K + k0 + 1];
-                double hi = (1.0 - ak) * qv[(long)(r0 + 1) * K + k0] + ak * qv[(long)(r0 + 1) * K + k0 + 1];
-                val = (1.0 - ar) * lo + ar * hi;
-            } else {
-                val = (1.0 - ak) * qv[k0] + ak * qv[k0 + 1];
-            }
-            acc += val / L2;
+    int ix = (int)(vi % g->nx), iy = (int)((vi / g->nx) % g->ny), iz = (int)(vi / ((long)g->nx * g->ny));
+    double X = X0 + ix * g->dx, Y = Y0 + iy * g->dy, Z = Z0 + iz * g->dz;
+    long v0, v1;
+    view_window(g, Z, &v0, &v1);
+    double acc = 0.0;
+    for (long v = v0; v < v1; v++) {
+        double beta = g->start_angle + 2.0 * M_PI * (double)v / (double)N;
+        double sx = g->sid * cos(beta), sy = g->sid * sin(beta);
+        double sz = g->z_start + g->feed * (double)v / (double)N;
+        double ddx = X - sx, ddy = Y - sy;
+        double L2 = ddx * ddx + ddy * ddy, L = sqrt(L2);
+        /* the ray of fan angle gamma points along beta + gamma + pi */
+        double gam = atan2(ddy, ddx) - beta - M_PI;
+        gam = gam - 2.0 * M_PI * floor((gam + M_PI) / (2.0 * M_PI));
+        double kf = gam / g->channel_pitch + (K - 1) / 2.0 - g->channel_offset;
+        if (!(kf >= 0.0 && kf <= K - 1)) continue;
+        double rf = 0.0;
+        if (R > 1) {
+            double w = (Z - sz) * g->sdd / L;
+            rf = w / g->row_pitch + (R - 1) / 2.0 - g->row_offset;
+            if (rf < 0.0) rf = 0.0;
+            if (rf > R - 1) rf = R - 1;
         }
-        img[vi] = acc * dbeta;
+        int k0 = (int)floor(kf), r0 = (int)floor(rf);
+        if (k0 > K - 2) k0 = K - 2 < 0 ? 0 : K - 2;
+        if (r0 > R - 2) r0 = R - 2 < 0 ? 0 : R - 2;
+        double ak = kf - k0, ar = rf - r0;
+        const double *qv = q + (long)v * R * K;
+        double val;
+        if (R > 1) {
+            double lo = (1.0 - ak) * qv[(long)r0 * K + k0] + ak * qv[(long)r0 * K + k0 + 1];
+            double hi = (1.0 - ak) * qv[(long)(r0 + 1) * K + k0] + ak * qv[(long)(r0 + 1) * K + k0 + 1];
+            val = (1.0 - ar) * lo + ar * hi;
+        } else {
+            val = (1.0 - ak) * qv[k0] + ak * qv[k0 + 1];
+        }
+        acc += val / L2;
     }
+    return acc * dbeta;
+}
+
+/* FBP backprojection of the filtered sinogram q [V][R][K] into img [nz][ny][nx]. */
+void or_fbp_backproject(const or_geometry *g, const double *q, double *img) {
+    const long nvox = (long)g->nx * g->ny * g->nz;
+#pragma omp parallel for schedule(dynamic, 256)
+    for (long vi = 0; vi < nvox; vi++) img[vi] = fbp_voxel(g, q, vi);
+}
+
+/* The same backprojection at n listed voxels (index iz*ny*nx + iy*nx + ix) only:
+ * out[i] = img[vox[i]]. */
+void or_fbp_backproject_at(const or_geometry *g, const double *q, const int64_t *vox, long n, double *out) {
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long i = 0; i < n; i++) out[i] = fbp_voxel(g, q, vox[i]);
 }
 
 /* FBP image [nz][ny][nx] of the line-integral sinogram p [V][R][K]. */

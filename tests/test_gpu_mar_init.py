@@ -183,3 +183,37 @@ def test_mar_init_argument_errors(pkg):
     fresh = pkg.from_case(case)
     with pytest.raises(pkg.DeamError):
         fresh.log_sinogram()                                # no data yet
+
+
+def test_c2_full_size_sampled(pkg):
+    # The MAR initialisation's steps at the benchmark's full size (512x512x64,
+    # 5800 views x 16 x 816), as bench.py times them: log sinograms and the
+    # trace completion of every ray against the oracle, and the FBP of the
+    # completed high-kVp sinogram at 2000 seeded voxels against the oracle's
+    # FBP of the same sinogram at those voxels.
+    import oracle
+    dev = torch.device("cuda")
+    case = synth.make_case("c2")
+    d, metal = synth.measure(case, device=dev, seed=1)
+    mask = (metal >= case.metal_threshold).to(torch.uint8)
+    del metal
+    g = pkg.from_case(case)
+    g.set_data(d)
+    g.set_metal_mask(mask, "ray")
+    O = oracle.from_case(case)
+    p = g.log_sinogram()
+    po = O.log_sinogram(d.cpu().double().numpy(), 1.0)
+    for j in range(2):
+        assert _rel(p[j].cpu().numpy(), po[j]) < 1e-6
+    del po
+    bits = O.mask_bits(mask.cpu().numpy())
+    ph = p[1].contiguous()
+    li = g.complete_trace(ph, 1)
+    li_o = O.complete_trace(ph.cpu().double().numpy(), bits, 1)
+    assert _rel(li.cpu().numpy(), li_o) < 1e-6
+    del li_o
+    img = g.fbp(li)
+    q = O.ramp_filter(li.cpu().double().numpy())
+    vox = np.sort(np.random.default_rng(5).choice(case.geo.n_voxels, size=2000, replace=False))
+    ref = O.fbp_backproject_at(q, vox)
+    assert _rel(img.reshape(-1)[torch.from_numpy(vox).to(dev)].cpu().numpy(), ref) < 1e-4

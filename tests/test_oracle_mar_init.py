@@ -284,3 +284,14 @@ def mar_calibration(case, O):
         mus.append([O.fbp(p[j])[:, roi].mean() for j in range(2)])
     (aL, aH), (bL, bH) = mus
     return np.array([aL, (bL - aL) / 0.3, aH, (bH - aH) / 0.3])
+
+
+def test_fbp_at_listed_voxels_equals_the_full_image():
+    # the voxel-list form (used for sampled parity at full size) is the same
+    # per-voxel sum as the full backprojection
+    geo = _geo2d(n=48, dx=2.0, V=360, K=200)
+    O = _oracle(geo)
+    q = O.ramp_filter(_line_integrals(geo, [_disk(-15.0, 5.0, 10.0, 0.02)]))
+    full = O.fbp_backproject(q).reshape(-1)
+    vox = np.array([0, 5, 100, 1151, 2303])
+    np.testing.assert_array_equal(O.fbp_backproject_at(q, vox), full[vox])
