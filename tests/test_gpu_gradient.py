@@ -170,3 +170,31 @@ def test_preconditioned_gradient_solver(pkg):
     assert len(F) >= 2 and np.all(np.diff(F) <= 0) and F[-1] < F[0]
     assert F[0] == pytest.approx(gpu.objective(c0.cuda()), rel=1e-12)
     assert F[-1] == pytest.approx(gpu.objective(c), rel=1e-12)
+
+
+def test_c1_full_size_gradient(pkg):
+    # At the differentiation workload's size (256x256x32 helical, 3480 views x
+    # 16 x 672): the adjoint kernel's gradient against the oracle's FP64
+    # gradient over every voxel, and the directional derivative of the GPU
+    # objective (central difference along a random sign pattern on the body)
+    # against <gradient, direction>.
+    import oracle
+    dev = torch.device("cuda")
+    case = synth.make_case("c1")
+    d, metal = synth.measure(case, device=dev, seed=1)
+    truth, _ = synth.voxelize(case, device=dev)
+    mask = (metal >= case.metal_threshold).to(torch.uint8)
+    c0 = synth.initial_image(case, truth).to(dev)
+    gpu = pkg.from_case(case)
+    gpu.set_data(d)
+    gpu.set_metal_mask(mask, "ray")
+    g, F = gpu.gradient(c0)
+    O = oracle.from_case(case)
+    go = O.gradient(c0.cpu().double().numpy(), d.cpu().double().numpy(), mask.cpu().numpy())
+    assert _rel(g.cpu().numpy(), go) < 1e-4
+    gen = torch.Generator(device="cpu").manual_seed(3)
+    v = (torch.randint(0, 2, c0.shape, generator=gen).float() * 2 - 1).to(dev) * (truth[..., :1] > 0.3)
+    eps = 1e-3
+    fd = (gpu.objective(c0 + eps * v) - gpu.objective(c0 - eps * v)) / (2 * eps)
+    dd = float((g.double() * v.double()).sum())
+    assert fd == pytest.approx(dd, rel=1e-3)
