@@ -83,3 +83,34 @@ def test_batch_rejects_bad_input(pkg):
     with pytest.raises(ValueError):
         batch.iterate([c0 for _, c0 in scans], 1)  # host images are refused by the binding
     batch.close()
+
+
+def test_full_batch_workload_persistent_plan(pkg):
+    # The batching workload at full size: 24 seeded scans (2D slices 128^2 to
+    # 512^2, 3D helical slabs 256^2x16 to 512^2x48, 180-1160 views, 1-3 metal
+    # inserts) in the persistent plan (one forward launch over all scans, one
+    # backprojection launch per slab class, captured in a CUDA graph) against
+    # each scan's own deam_iterate.
+    dev = torch.device("cuda")
+    scans, imgs = [], []
+    for case in synth.make_batch_cases(24):
+        d, metal = synth.measure(case, device=dev, seed=1)
+        truth, _ = synth.voxelize(case, device=dev)
+        g = pkg.from_case(case)
+        g.set_data(d)
+        g.set_metal_mask((metal >= case.metal_threshold).to(torch.uint8), "ray")
+        scans.append(g)
+        imgs.append(synth.initial_image(case, truth).to(dev))
+        del d, metal, truth
+    ref = []
+    for g, c0 in zip(scans, imgs):
+        c = c0.clone()
+        ref.append((c, g.iterate(c, 2)))
+    batch = pkg.DeamBatch(scans, autotune=False)
+    cb = [c.clone() for c in imgs]
+    H = batch.iterate(cb, 2)
+    assert batch.info()["plan"] == "persistent"
+    for i, (c, h) in enumerate(ref):
+        assert _rel(cb[i], c) < 1e-6, i
+        np.testing.assert_allclose(H[i], h, rtol=1e-7)
+    batch.close()
