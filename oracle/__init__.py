@@ -44,7 +44,7 @@ class Model(C.Structure):
 class MarParams(C.Structure):
     _fields_ = [("calib", C.c_double * 4), ("t_air", C.c_double), ("t_bone", C.c_double),
                 ("soft_value", C.c_double), ("count_floor", C.c_double), ("eps", C.c_double),
-                ("prior_spectrum", C.c_int)]
+                ("prior_spectrum", C.c_int), ("prior_smooth", C.c_int)]
 
 
 class Tap(C.Structure):
@@ -100,6 +100,7 @@ def lib():
             "or_fbp": (None, [G, pd, pd]),
             "or_fbp_backproject_at": (None, [G, pd, pi64, l, pd]),
             "or_prior": (None, [l, pd, d, d, d, pd]),
+            "or_smooth_inplane": (None, [i, i, i, pd, i]),
             "or_decompose": (None, [l, pd, pd, pd, pd]),
             "or_mar_init": (None, [G, M, pd, pu8, P(MarParams), pd, pd, pd, pd, pd]),
         }
@@ -324,12 +325,13 @@ class Oracle:
         return out
 
     def mar_init(self, d, mask, calib, t_air, t_bone, soft_value, count_floor=1.0, eps=1e-3,
-                 prior_spectrum=1, prior=None):
+                 prior_spectrum=1, prior=None, prior_smooth=1):
         """(c [nz,ny,nx,2], prior, mu_L, mu_H) of the MAR initialisation; `prior`
         (optional) replaces the thresholded prior image."""
         d, mk = self._dm(d, mask)
         P = MarParams((C.c_double * 4)(*[float(x) for x in np.asarray(calib).reshape(4)]), float(t_air),
-                      float(t_bone), float(soft_value), float(count_floor), float(eps), int(prior_spectrum))
+                      float(t_bone), float(soft_value), float(count_floor), float(eps), int(prior_spectrum),
+                      int(prior_smooth))
         shp = self.img_shape[:3]
         pin = None if prior is None else _f64(_np(prior)).reshape(shp)
         c = np.zeros(self.img_shape)
@@ -337,6 +339,15 @@ class Oracle:
         self.L.or_mar_init(C.byref(self.g), C.byref(self.m), _p(d), _p(mk, C.c_uint8), C.byref(P),
                            _p(pin) if pin is not None else C.POINTER(C.c_double)(), _p(c), _p(po), _p(mL), _p(mH))
         return c, po, mL, mH
+
+
+def smooth_inplane(f, passes=1):
+    """n passes of the in-plane [1,2,1]/4 x [1,2,1]/4 smoothing (edges replicated)
+    of an image [nz, ny, nx]."""
+    f = _f64(_np(f)).copy()
+    nz, ny, nx = f.shape
+    lib().or_smooth_inplane(nx, ny, nz, _p(f), int(passes))
+    return f
 
 
 def prior_image(f, t_air, t_bone, soft_value):

@@ -13,7 +13,8 @@
  * Readings where the paper is silent (each is a parameter or a stated choice):
  *  - sinogram p_j(y) = ln(I0_j(y) / max(d_j(y), floor)), I0_j(y) = sum_E I0_j(E) b(k);
  *  - the prior comes from the FBP of the chosen spectrum's sinogram with the trace
- *    completed by plain linear interpolation (prior == 1), thresholded into
+ *    completed by plain linear interpolation (prior == 1), filtered by n passes
+ *    of an in-plane [1,2,1]/4 smoothing in x and y, and thresholded into
  *    0 (f < t_air), a soft-tissue value (t_air <= f < t_bone) and f (f >= t_bone);
  *  - NMAR normalises by max(prior projection, eps) and interpolates linearly along
  *    the channels of each (view, row) between the nearest rays off the trace of
@@ -45,6 +46,7 @@ typedef struct {
     double t_air, t_bone, soft_value;
     double count_floor, eps;
     int prior_spectrum; /* 0: L, 1: H */
+    int prior_smooth;   /* passes of the in-plane [1,2,1]/4 x [1,2,1]/4 filter before thresholding */
 } or_mar_params;
 
 /* Line-integral sinograms of both spectra: p [2][V][R][K]. */
@@ -231,6 +233,33 @@ void or_fbp(const or_geometry *g, const double *p, double *img) {
     free(q);
 }
 
+/* The "filtering" of the prior (Sec. 2.2 figure caption; reading: a separable
+ * in-plane [1,2,1]/4 smoothing in x and y, edges replicated), applied n times
+ * to f [nz][ny][nx] in place. */
+void or_smooth_inplane(int nx, int ny, int nz, double *f, int n) {
+    const long nvox = (long)nx * ny * nz;
+    double *t = (double *)malloc(sizeof(double) * nvox);
+    for (int pass = 0; pass < n; pass++) {
+        for (long i = 0; i < nvox; i++) {
+            int ix = (int)(i % nx), iy = (int)((i / nx) % ny);
+            long base = i - ix - (long)iy * nx;
+            double acc = 0.0;
+            for (int b = -1; b <= 1; b++) {
+                int y = iy + b < 0 ? 0 : (iy + b >= ny ? ny - 1 : iy + b);
+                double wy = b == 0 ? 0.5 : 0.25;
+                for (int a = -1; a <= 1; a++) {
+                    int x = ix + a < 0 ? 0 : (ix + a >= nx ? nx - 1 : ix + a);
+                    double wx = a == 0 ? 0.5 : 0.25;
+                    acc += wx * wy * f[base + (long)y * nx + x];
+                }
+            }
+            t[i] = acc;
+        }
+        memcpy(f, t, sizeof(double) * nvox);
+    }
+    free(t);
+}
+
 /* Prior image by thresholding the single-energy FBP image f. */
 void or_prior(long nvox, const double *f, double t_air, double t_bone, double soft, double *prior) {
     for (long i = 0; i < nvox; i++) prior[i] = f[i] < t_air ? 0.0 : (f[i] < t_bone ? soft : f[i]);
@@ -270,6 +299,7 @@ void or_mar_init(const or_geometry *g, const or_model *m, const double *d, const
         int j = P->prior_spectrum ? 1 : 0;
         or_complete_trace(g, p + j * n, NULL, mask, j, P->eps, t);
         or_fbp(g, t, f);
+        or_smooth_inplane(g->nx, g->ny, g->nz, f, P->prior_smooth);
         or_prior(nvox, f, P->t_air, P->t_bone, P->soft_value, prior);
     }
     for (long i = 0; i < nvox; i++) c2[2 * i] = prior[i];

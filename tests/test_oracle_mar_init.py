@@ -295,3 +295,23 @@ def test_fbp_at_listed_voxels_equals_the_full_image():
     full = O.fbp_backproject(q).reshape(-1)
     vox = np.array([0, 5, 100, 1151, 2303])
     np.testing.assert_array_equal(O.fbp_backproject_at(q, vox), full[vox])
+
+
+def test_prior_smoothing_closed_forms():
+    # the in-plane [1,2,1]/4 filter: a delta spreads into the binomial kernel
+    # ([1,2,1] x [1,2,1] / 16 after one pass, [1,4,6,4,1] x [1,4,6,4,1] / 256
+    # after two), constants and linear ramps are kept, slices do not mix
+    f = np.zeros((3, 9, 11))
+    f[1, 4, 5] = 1.0
+    one = oracle.smooth_inplane(f, 1)
+    k1 = np.outer([1, 2, 1], [1, 2, 1]) / 16.0
+    np.testing.assert_allclose(one[1, 3:6, 4:7], k1, rtol=0, atol=1e-15)
+    assert abs(one[1].sum() - 1.0) < 1e-15 and not one[0].any() and not one[2].any()
+    two = oracle.smooth_inplane(f, 2)
+    b = np.array([1, 4, 6, 4, 1])
+    np.testing.assert_allclose(two[1, 2:7, 3:8], np.outer(b, b) / 256.0, rtol=0, atol=1e-15)
+    const = np.full((2, 5, 6), 0.7)
+    np.testing.assert_allclose(oracle.smooth_inplane(const, 3), const, rtol=1e-15)
+    ramp = np.broadcast_to(0.1 * np.arange(11.0)[None, None, :] + 0.3 * np.arange(9.0)[None, :, None], (2, 9, 11))
+    out = oracle.smooth_inplane(ramp, 1)
+    np.testing.assert_allclose(out[:, 1:-1, 1:-1], ramp[:, 1:-1, 1:-1], rtol=1e-14)
