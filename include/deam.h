@@ -197,7 +197,8 @@ int deam_backprojected_sums(deam_ctx *ctx, const float *c, float *sums, double *
  * interpolate linearly along the channels, multiply back), reconstructed by
  * filtered backprojection, and split into the basis components by the
  * image-domain decomposition of Eq. (4).  The prior thresholds a
- * single-energy FBP image (Sec. 2.2: "prior image by thresholding").
+ * single-energy FBP image, filtered (Sec. 2.2: the prior is obtained by
+ * thresholding and filtering).
  * FBP: equiangular fan-beam filtered backprojection on the curved detector
  * (pre-weight SID cos(gamma), the discrete equiangular ramp kernel), extended
  * to the helix FDK-style (cone pre-weight SDD / sqrt(SDD^2 + w^2); each voxel
@@ -215,7 +216,9 @@ typedef struct deam_mar_params {
     double count_floor;    /* counts: d~ is floored here before the log (> 0; 1 is typical) */
     double eps;            /* NMAR: the prior projection is floored here before dividing (> 0) */
     int prior_spectrum;    /* single-energy image of the prior: 0 = L, 1 = H */
-    int reserved[7];       /* zero */
+    int prior_smooth;      /* passes (0..16) of an in-plane [1,2,1]/4 x [1,2,1]/4 smoothing of that
+                              image before the thresholds (the prior's "filtering"; edges replicated) */
+    int reserved[6];       /* zero */
 } deam_mar_params;
 
 /* Line-integral sinograms p_j(y) = ln(I0_j(y) / max(d~_j(y), count_floor)),

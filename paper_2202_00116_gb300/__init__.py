@@ -55,7 +55,7 @@ class deam_options(C.Structure):
 class deam_mar_params(C.Structure):
     _fields_ = [("calib", C.c_double * 4), ("t_air", C.c_double), ("t_bone", C.c_double),
                 ("soft_value", C.c_double), ("count_floor", C.c_double), ("eps", C.c_double),
-                ("prior_spectrum", C.c_int), ("reserved", C.c_int * 7)]
+                ("prior_spectrum", C.c_int), ("prior_smooth", C.c_int), ("reserved", C.c_int * 6)]
 
 
 class DeamError(RuntimeError):
@@ -334,14 +334,14 @@ class Deam:
         return img[0] if single else img
 
     def mar_init(self, calib, t_air, t_bone, soft_value, count_floor=1.0, eps=1e-3, prior_spectrum=1,
-                 prior=None):
+                 prior=None, prior_smooth=1):
         """(c^0 [nz, ny, nx, 2], prior [nz, ny, nx], mu [2, nz, ny, nx]): NMAR-corrected
         FBP images of both spectra split by Eq. (4) with calib = (mu~_1L, mu~_2L,
         mu~_1H, mu~_2H); `prior` replaces the thresholded prior image."""
         torch = self.torch
         P = deam_mar_params((C.c_double * 4)(*[float(x) for x in np.asarray(calib, dtype=np.float64).reshape(4)]),
                             float(t_air), float(t_bone), float(soft_value), float(count_floor), float(eps),
-                            int(prior_spectrum))
+                            int(prior_spectrum), int(prior_smooth))
         c = torch.empty(self.img_shape, dtype=torch.float32, device=self.device)
         pr = torch.empty(self.img_shape[:3], dtype=torch.float32, device=self.device)
         mu = torch.empty((2,) + self.img_shape[:3], dtype=torch.float32, device=self.device)

@@ -209,6 +209,28 @@ __global__ void fbp_kernel(const float* __restrict__ q, long long nrays, const f
     for (int s = 0; s < NS; ++s) img[s * nvox + vi] = acc[s] * F.dbeta;
 }
 
+// One pass of the in-plane [1,2,1]/4 x [1,2,1]/4 smoothing (edges replicated).
+__global__ void smooth_kernel(const float* __restrict__ f, int nx, int ny, long long n, float* __restrict__ out) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int ix = (int)(i % nx), iy = (int)((i / nx) % ny);
+        const long long base = i - ix - (long long)iy * nx;
+        float acc = 0.f;
+#pragma unroll
+        for (int b = -1; b <= 1; ++b) {
+            const int y = min(max(iy + b, 0), ny - 1);
+            const float wy = b == 0 ? 0.5f : 0.25f;
+#pragma unroll
+            for (int a = -1; a <= 1; ++a) {
+                const int x = min(max(ix + a, 0), nx - 1);
+                const float wx = a == 0 ? 0.5f : 0.25f;
+                acc = fmaf(wx * wy, f[base + (long long)y * nx + x], acc);
+            }
+        }
+        out[i] = acc;
+    }
+}
+
 __global__ void prior_kernel(const float* __restrict__ f, long long n, float t_air, float t_bone, float soft,
                              float* __restrict__ prior) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -414,6 +436,7 @@ int deam_mar_init(deam_ctx* ctx, const deam_mar_params* P, const float* prior_in
     if (!(isfinite(P->count_floor) && P->count_floor > 0.0)) return fail(DEAM_ERR_ARG, "count_floor must be > 0");
     if (!(isfinite(P->eps) && P->eps > 0.0)) return fail(DEAM_ERR_ARG, "eps must be > 0");
     if (P->prior_spectrum != 0 && P->prior_spectrum != 1) return fail(DEAM_ERR_ARG, "prior_spectrum must be 0 or 1");
+    if (P->prior_smooth < 0 || P->prior_smooth > 16) return fail(DEAM_ERR_ARG, "prior_smooth must be 0..16");
     if (ctx->geo.n_channels < 2 || ctx->geo.n_channels > kMaxFbpChannels)
         return fail(DEAM_ERR_ARG, "FBP needs 2 to 3072 channels (the ramp filter stages a row in shared memory)");
     DevGuard dg(ctx->device);
@@ -421,10 +444,11 @@ int deam_mar_init(deam_ctx* ctx, const deam_mar_params* P, const float* prior_in
     const long long nr = ctx->nrays, nv = ctx->nvox;
     float *p = nullptr, *t = nullptr, *img = nullptr;
     float2* l = nullptr;
-    // p: both sinograms; t: completed sinograms (filtered in place); img: f | prior | mu_L | mu_H
+    // p: both sinograms; t: completed sinograms (filtered in place);
+    // img: f | prior | mu_L | mu_H | smoothing scratch
     CK(cudaMallocAsync((void**)&p, sizeof(float) * 2 * nr, s));
     cudaError_t e = cudaMallocAsync((void**)&t, sizeof(float) * 2 * nr, s);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&img, sizeof(float) * 4 * nv, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&img, sizeof(float) * 5 * nv, s);
     if (e == cudaSuccess) e = cudaMallocAsync((void**)&l, sizeof(float2) * nr, s);
     auto release = [&]() {
         if (p) cudaFreeAsync(p, s);
@@ -451,7 +475,15 @@ int deam_mar_init(deam_ctx* ctx, const deam_mar_params* P, const float* prior_in
             if (rc != DEAM_OK) return rc;
             rc = fbp(ctx, t, 1, t, f, s);
             if (rc != DEAM_OK) return rc;
-            prior_kernel<<<grid_for(nv, 256), 256, 0, s>>>(f, nv, (float)P->t_air, (float)P->t_bone,
+            // filtering: passes ping-pong between f and the scratch image
+            float* a = f;
+            float* b = img + 4 * nv;  // smoothing scratch
+            for (int pass = 0; pass < P->prior_smooth; ++pass) {
+                smooth_kernel<<<grid_for(nv, 256), 256, 0, s>>>(a, ctx->geo.nx, ctx->geo.ny, nv, b);
+                CK(cudaGetLastError());
+                std::swap(a, b);
+            }
+            prior_kernel<<<grid_for(nv, 256), 256, 0, s>>>(a, nv, (float)P->t_air, (float)P->t_bone,
                                                            (float)P->soft_value, prior);
             CK(cudaGetLastError());
         }

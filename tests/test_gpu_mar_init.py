@@ -6,7 +6,8 @@ FP32 roundings per element (relative L2 <= 1e-6).  FBP: the ramp sums and the
 backprojection sums are compensated, so the error is set by the FP32 geometry
 (fan angle from atan2f, ~1e-7 rad, i.e. ~1e-4 of a channel, times the
 filtered sinogram's channel-to-channel variation): relative L2 <= 1e-4 over
-the image.  The prior's thresholds are decisions taken in FP32 on the GPU:
+the image.  The prior (one pass of the in-plane smoothing, then the thresholds) is
+decided in FP32 on the GPU:
 the full pipeline is compared with the oracle run on the GPU's prior, and the
 GPU's prior is checked against the oracle's classification, which may differ
 only where the oracle's FBP value lies within 1e-4 (relative) of a threshold."""
@@ -133,7 +134,7 @@ def test_mar_init_matches_oracle(pkg, name):
     assert _rel(c.cpu().numpy(), co) < 1e-4
     # the GPU's threshold decisions against the oracle's own prior
     bits = O.mask_bits(mask.numpy())
-    f = O.fbp(O.complete_trace(O.log_sinogram(dn)[1], bits, 1))
+    f = oracle.smooth_inplane(O.fbp(O.complete_trace(O.log_sinogram(dn)[1], bits, 1)), 1)
     _, po_own, _, _ = O.mar_init(dn, mask.numpy(), calib, **MAR)
     pg = prior.cpu().double().numpy()
 
@@ -180,6 +181,8 @@ def test_mar_init_argument_errors(pkg):
         g.mar_init([1.0, 2.0, 2.0, 4.0], **MAR)             # singular calibration
     with pytest.raises(pkg.DeamError):
         g.mar_init([0.02, 0.04, 0.018, 0.03], count_floor=0.0, **MAR)
+    with pytest.raises(pkg.DeamError):
+        g.mar_init([0.02, 0.04, 0.018, 0.03], prior_smooth=17, **MAR)
     fresh = pkg.from_case(case)
     with pytest.raises(pkg.DeamError):
         fresh.log_sinogram()                                # no data yet
