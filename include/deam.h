@@ -122,7 +122,9 @@ int deam_init(const deam_geometry *geom, const deam_spectra *spectra, const deam
               const deam_options *opts, deam_ctx **out);
 
 /* Store the measurements d (host or device, float32 [2][V][R][K], counts) as the
- * nonnegative substitution d~ = max(d, 0) (Sec. 2.1). */
+ * nonnegative substitution d~ = max(d, 0) (Sec. 2.1).  A host buffer may be
+ * reused as soon as the call returns (the call waits for its copy); a device
+ * buffer is read on `stream`. */
 int deam_set_data(deam_ctx *ctx, const float *d, void *stream);
 
 /* Set the metal trace (Sec. 2.1: rays with T(y) >= t are "metal").  kind =

@@ -407,6 +407,7 @@ int deam_set_data(deam_ctx* ctx, const float* d, void* stream) {
     } else {
         CK(cudaMemcpyAsync(ctx->dt, d, sizeof(float) * n, cudaMemcpyHostToDevice, s));
         CK(deam::launch_clamp_copy(ctx->dt, ctx->dt, n, s));
+        CK(cudaStreamSynchronize(s));  // the caller's host buffer is released on return
     }
     ctx->has_data = true;
     return DEAM_OK;
