@@ -439,6 +439,7 @@ int deam_set_metal_mask(deam_ctx* ctx, const void* m, int kind, void* stream) {
         A.mask_out = ctx->mask;
         A.threshold = (float)ctx->threshold;
         CK(deam::launch_forward(deam::FWD_MASK, ctx->G, ctx->S, A, ctx->n_fwd_blocks, s));
+        if (!dev) CK(cudaStreamSynchronize(s));  // the caller's host buffer is released on return
     } else {
         return fail(DEAM_ERR_ARG, "unknown mask kind");
     }
