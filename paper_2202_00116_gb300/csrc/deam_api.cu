@@ -69,6 +69,13 @@ int deam::set_error(int code, const char* msg) { return fail(code, msg); }
         }                                                                                      \
     } while (0)
 
+// Device-only arguments are checked on the host: a host pointer would otherwise
+// fail inside the runtime or fault in a kernel and leave the context unusable.
+#define NEED_DEVICE(p, name)                                                         \
+    do {                                                                             \
+        if ((p) && !is_device_ptr(p)) return fail(DEAM_ERR_ARG, name " must be device memory"); \
+    } while (0)
+
 #define CHECK_CTX(ctx)                                                              \
     do {                                                                            \
         if (!(ctx)) return fail(DEAM_ERR_ARG, "null context");                      \
@@ -451,6 +458,7 @@ int deam_get_metal_mask(deam_ctx* ctx, uint8_t* mask, void* stream) {
     CHECK_CTX(ctx);
     if (!mask) return fail(DEAM_ERR_ARG, "mask must not be NULL");
     DeviceGuard dg(ctx->device);
+    NEED_DEVICE(mask, "mask");
     CK(cudaMemcpyAsync(mask, ctx->mask, (size_t)ctx->nrays, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
     return DEAM_OK;
 }
@@ -459,6 +467,9 @@ int deam_forward(deam_ctx* ctx, const float* c, float* l, float* g, void* stream
     CHECK_CTX(ctx);
     if (!c || (!l && !g)) return fail(DEAM_ERR_ARG, "need c and at least one of l, g");
     DeviceGuard dg(ctx->device);
+    NEED_DEVICE(c, "c");
+    NEED_DEVICE(l, "l");
+    NEED_DEVICE(g, "g");
     cudaStream_t s = (cudaStream_t)stream;
     int rc = build_layouts(ctx, (const float2*)c, nullptr, 0, s);
     if (rc != DEAM_OK) return rc;
@@ -473,6 +484,8 @@ int deam_backproject(deam_ctx* ctx, const float* y, float* img, void* stream) {
     CHECK_CTX(ctx);
     if (!y || !img) return fail(DEAM_ERR_ARG, "y and img must not be NULL");
     DeviceGuard dg(ctx->device);
+    NEED_DEVICE(y, "y");
+    NEED_DEVICE(img, "img");
     deam::BwdArgs B{};
     B.rays2 = (const float2*)y;
     B.img = (float2*)img;
@@ -502,6 +515,8 @@ int deam_ray_terms(deam_ctx* ctx, const float* c, float* payload, double* F, voi
     if (!c || !payload) return fail(DEAM_ERR_ARG, "c and payload must not be NULL");
     if (!ctx->has_data) return fail(DEAM_ERR_STATE, "deam_set_data has not been called");
     DeviceGuard dg(ctx->device);
+    NEED_DEVICE(c, "c");
+    NEED_DEVICE(payload, "payload");
     return ray_terms(ctx, (const float2*)c, (float4*)payload, F, ctx->scal, (cudaStream_t)stream);
 }
 
@@ -510,6 +525,7 @@ int deam_objective(deam_ctx* ctx, const float* c, double* out, void* stream) {
     if (!c || !out) return fail(DEAM_ERR_ARG, "c and out must not be NULL");
     if (!ctx->has_data) return fail(DEAM_ERR_STATE, "deam_set_data has not been called");
     DeviceGuard dg(ctx->device);
+    NEED_DEVICE(c, "c");
     int rc = ray_terms(ctx, (const float2*)c, ctx->payload, out, ctx->scal, (cudaStream_t)stream);
     if (rc == DEAM_OK && !isfinite(*out)) return fail(DEAM_ERR_NUMERIC, "objective is not finite");
     return rc;
@@ -598,6 +614,8 @@ int deam_backprojected_sums(deam_ctx* ctx, const float* c, float* sums, double* 
     if (!c || !sums) return fail(DEAM_ERR_ARG, "c and sums must not be NULL");
     if (!ctx->has_data) return fail(DEAM_ERR_STATE, "deam_set_data has not been called");
     DeviceGuard dg(ctx->device);
+    NEED_DEVICE(c, "c");
+    NEED_DEVICE(sums, "sums");
     cudaStream_t s = (cudaStream_t)stream;
     int rc = ray_terms(ctx, (const float2*)c, ctx->payload, nullptr, ctx->scal, s);
     if (rc != DEAM_OK) return rc;
@@ -620,6 +638,8 @@ int deam_gradient(deam_ctx* ctx, const float* c, float* grad, double* F, void* s
     if (!c || !grad) return fail(DEAM_ERR_ARG, "c and grad must not be NULL");
     if (!ctx->has_data) return fail(DEAM_ERR_STATE, "deam_set_data has not been called");
     DeviceGuard dg(ctx->device);
+    NEED_DEVICE(c, "c");
+    NEED_DEVICE(grad, "grad");
     cudaStream_t s = (cudaStream_t)stream;
     // per-ray terms recomputed from c (nothing per energy bin is stored), then
     // the gather backprojection of D = sum_j (r_j - 1) S_ij gives b^ - b~
@@ -642,6 +662,7 @@ int deam_penalty(deam_ctx* ctx, const float* c, double* R, void* stream) {
     CHECK_CTX(ctx);
     if (!c || !R) return fail(DEAM_ERR_ARG, "c and R must not be NULL");
     DeviceGuard dg(ctx->device);
+    NEED_DEVICE(c, "c");
     cudaStream_t s = (cudaStream_t)stream;
     const deam_geometry& g = ctx->geo;
     CK(deam::launch_penalty((const float2*)c, g.nx, g.ny, g.nz, (float)g.dx, (float)g.dy, (float)g.dz,
@@ -658,6 +679,8 @@ int deam_basis_images(deam_ctx* ctx, const float* c, const double* coef, int n, 
     for (int e = 0; e < 2 * n; ++e)
         if (!isfinite(coef[e])) return fail(DEAM_ERR_ARG, "coefficients must be finite");
     DeviceGuard dg(ctx->device);
+    NEED_DEVICE(c, "c");
+    NEED_DEVICE(out, "out");
     cudaStream_t s = (cudaStream_t)stream;
     if (!ctx->coef) CK(dalloc(&ctx->coef, 256));
     std::vector<float2> ab(n);

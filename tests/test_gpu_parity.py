@@ -216,6 +216,27 @@ def test_zero_iterations_and_errors(pkg):
         gpu.iterate(c[:, :5].contiguous(), 1)  # wrong shape caught in the binding
 
 
+def test_host_pointers_to_device_only_arguments_are_rejected(pkg):
+    # a host buffer where device memory is required is an argument error caught
+    # on the host; the context stays usable afterwards
+    import ctypes as C
+    case, d, mask, M, c0 = case_data("t2d")
+    gpu = pkg.from_case(case)
+    gpu.set_data(d.cuda())
+    gpu.set_metal_mask(mask.cuda(), "ray")
+    L = pkg.lib()
+    host_c = c0.contiguous()
+    l_dev = torch.empty(gpu.ray_shape + (2,), device="cuda")
+    rc = L.deam_forward(gpu._h, C.c_void_p(host_c.data_ptr()), C.c_void_p(l_dev.data_ptr()), None, None)
+    assert rc == pkg.DEAM_ERR_ARG and b"device memory" in L.deam_last_error()
+    host_l = torch.empty(gpu.ray_shape + (2,))
+    rc = L.deam_forward(gpu._h, C.c_void_p(c0.cuda().data_ptr()), C.c_void_p(host_l.data_ptr()), None, None)
+    assert rc == pkg.DEAM_ERR_ARG
+    host_m = torch.empty(gpu.ray_shape, dtype=torch.uint8)
+    assert L.deam_get_metal_mask(gpu._h, C.c_void_p(host_m.data_ptr()), None) == pkg.DEAM_ERR_ARG
+    assert gpu.objective(c0.cuda()) > 0          # still usable
+
+
 def test_single_voxel_closed_form_on_gpu(pkg):
     # one voxel, one ray, one bin: c' - c* = (1 - mu.L/Z)(c - c*) with Z = (mu1+mu2) L
     geo = synth.Geometry(1, 1, 1, 1, 2.0, 3.0, 4.0, 0.0, 0.0, 0.0, 570.0, 1040.0, 1, 8, 0.0, 0.0, 0.0,
