@@ -150,6 +150,16 @@ __global__ void __launch_bounds__(kThreads) objective_image_kernel(const ScanGeo
 
 bool finite_pos(double x) { return isfinite(x) && x > 0.0; }
 
+// Device (or managed) memory: a host buffer here would fault the kernel.
+bool on_device(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
 }  // namespace
 
 extern "C" int deam_objective_noalloc(const deam_geometry* geom, const deam_spectra* spectra,
@@ -157,6 +167,8 @@ extern "C" int deam_objective_noalloc(const deam_geometry* geom, const deam_spec
                                       const uint8_t* mask, double* F, void* stream) {
     if (!geom || !spectra || !basis || !c || !d || !F)
         return err(DEAM_ERR_ARG, "deam_objective_noalloc: geometry, spectra, basis, c, d and F must not be NULL");
+    if (!on_device(c) || !on_device(d) || !on_device(F) || (mask && !on_device(mask)))
+        return err(DEAM_ERR_ARG, "deam_objective_noalloc: c, d, mask and F must be device memory");
     const deam_geometry& g = *geom;
     if (g.nx < 1 || g.ny < 1 || g.nz < 1 || g.n_views < 1 || g.n_rows < 1 || g.n_channels < 1 ||
         g.views_per_rotation < 1 || !finite_pos(g.dx) || !finite_pos(g.dy) || !finite_pos(g.dz) ||

@@ -63,3 +63,25 @@ def test_objective_noalloc_rejects_oversized_scans(pkg):
         pkg.objective_noalloc(geo, case.I0, case.mu, dummy, dummy, None, F)
     assert e.value.code == pkg.DEAM_ERR_ARG
     assert "134217728" in str(e.value)
+
+
+def test_objective_noalloc_rejects_host_buffers(pkg):
+    # called through the C ABI directly (the binding refuses host tensors
+    # itself): a host buffer is an argument error, not a device fault
+    import ctypes as C
+    case = synth.make_case("t2d")
+    g = case.geo
+    geo = pkg.deam_geometry(int(g.kind), g.nx, g.ny, g.nz, g.dx, g.dy, g.dz, g.cx, g.cy, g.cz, g.sid, g.sdd,
+                            g.n_views, g.views_per_rotation, g.start_angle, g.feed, g.z_start, g.n_rows,
+                            g.row_pitch, g.n_channels, g.channel_pitch, g.channel_offset, g.row_offset)
+    I0 = np.ascontiguousarray(case.I0, dtype=np.float64)
+    mu = np.ascontiguousarray(case.mu, dtype=np.float64)
+    P = C.POINTER(C.c_double)
+    sp = pkg.deam_spectra(I0.shape[1], P(), I0.ctypes.data_as(P), P())
+    ba = pkg.deam_basis(mu.shape[1], mu.ctypes.data_as(P))
+    c_host = torch.zeros((g.nz, g.ny, g.nx, 2))
+    d_dev = torch.zeros((2, g.n_views, g.n_rows, g.n_channels), device="cuda")
+    F = torch.zeros(1, dtype=torch.float64, device="cuda")
+    rc = pkg.lib().deam_objective_noalloc(C.byref(geo), C.byref(sp), C.byref(ba), C.c_void_p(c_host.data_ptr()),
+                                          C.c_void_p(d_dev.data_ptr()), None, C.c_void_p(F.data_ptr()), None)
+    assert rc == pkg.DEAM_ERR_ARG and b"device memory" in pkg.lib().deam_last_error()
