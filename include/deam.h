@@ -341,7 +341,9 @@ int deam_batch_destroy(deam_batch *b);
 int deam_objective_noalloc(const deam_geometry *geom, const deam_spectra *spectra, const deam_basis *basis,
                            const float *c, const float *d, const uint8_t *mask, double *F, void *stream);
 
-/* Release the context and its device buffers (waits for its work). NULL is a no-op. */
+/* Release the context and its device buffers (waits for its work). NULL is a no-op.
+ * A context held by a live batch is not released: DEAM_ERR_STATE (destroy the
+ * batch first). */
 int deam_destroy(deam_ctx *ctx);
 
 /* Message of the last error on the calling thread ("" if none). */

@@ -400,8 +400,9 @@ class Deam:
         return list(ms), list(n)
 
     def close(self):
+        """Release the context (raises DeamError while a live DeamBatch holds it)."""
         if getattr(self, "_h", None):
-            lib().deam_destroy(self._h)
+            _check(lib().deam_destroy(self._h))
             self._h = None
 
     def __del__(self):

@@ -390,6 +390,7 @@ int deam_init(const deam_geometry* geom, const deam_spectra* spectra, const deam
 
 int deam_destroy(deam_ctx* ctx) {
     if (!ctx) return DEAM_OK;
+    if (ctx->batch_refs > 0) return fail(DEAM_ERR_STATE, "the context is part of a live batch: destroy the batch first");
     DeviceGuard dg(ctx->device);
     cudaDeviceSynchronize();
     free_ctx(ctx);

@@ -35,6 +35,7 @@ constexpr int kSlabs[3] = {2, 8, 16};     // slab classes
 struct deam_batch {
     int n = 0, device = 0, autotune = 1;
     std::vector<deam_ctx*> ctx;
+    bool holds_refs = false;  // the contexts' batch_refs count this batch
     deam::Geo* geos = nullptr;
     deam::Spec* specs = nullptr;
     deam::FwdArgs* fargs = nullptr;
@@ -76,6 +77,8 @@ struct deam_batch {
     } while (0)
 
 static void free_batch(deam_batch* b) {
+    if (b->holds_refs)
+        for (deam_ctx* x : b->ctx) --x->batch_refs;
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->cs) cudaStreamDestroy(b->cs);
     for (cudaStream_t q : b->br)
@@ -459,6 +462,8 @@ int deam_batch_create(deam_ctx* const* ctxs, int n, int autotune, deam_batch** o
     }
     // default shapes when not tuned: the single-scan kernels' shapes
     b->fshape = 1;
+    for (deam_ctx* x : b->ctx) ++x->batch_refs;
+    b->holds_refs = true;
     *out = b;
     return DEAM_OK;
 }

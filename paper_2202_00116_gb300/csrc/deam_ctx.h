@@ -19,6 +19,7 @@ struct deam_ctx {
     int fwd_mode = deam::FWD_DEAM;     // FWD_DEAM_F32 for the plain-FP32 variant
     double i0tot[2] = {0.0, 0.0};      // sum_E I0_j(E) (MAR initialisation's log sinograms)
     bool has_data = false, mask_set = false, failed = false;
+    int batch_refs = 0;                // live batches holding this context (deam_destroy refuses)
     long long nrays = 0, nvox = 0, skipped_last = 0;
     int n_fwd_blocks = 0, n_slabs = 0, slab = 16;
     // device buffers

@@ -114,3 +114,15 @@ def test_full_batch_workload_persistent_plan(pkg):
         assert _rel(cb[i], c) < 1e-6, i
         np.testing.assert_allclose(H[i], h, rtol=1e-7)
     batch.close()
+
+
+def test_context_in_a_live_batch_is_not_destroyed(pkg):
+    scans = _scans(pkg, 2)
+    batch = pkg.DeamBatch([g for g, _ in scans], autotune=False)
+    with pytest.raises(pkg.DeamError) as e:
+        scans[0][0].close()
+    assert e.value.code == pkg.DEAM_ERR_STATE
+    imgs = [c0.clone().cuda() for _, c0 in scans]
+    assert batch.iterate(imgs, 1).shape == (2, 1)      # the batch still works
+    batch.close()
+    scans[0][0].close()                                # now allowed
