@@ -306,27 +306,34 @@ int deam_init(const deam_geometry* geom, const deam_spectra* spectra, const deam
     // ---- device buffers ----
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const size_t volx = (size_t)nx * (nz + 2) * (ny + 1), voly = (size_t)ny * (nz + 2) * (nx + 1);
+    // allocations stop at the first failure (no further large requests once
+    // the device has refused one)
     cudaError_t e = cudaSuccess;
+#define DEAM_ALLOC(p, n)                        \
+    do {                                        \
+        if (e == cudaSuccess) e = dalloc(&(p), (n)); \
+    } while (0)
+    DEAM_ALLOC(ctx->view4, g.n_views);
+    DEAM_ALLOC(ctx->view_z, g.n_views);
+    DEAM_ALLOC(ctx->ip4, (size_t)g.n_views * g.n_channels);
+    DEAM_ALLOC(ctx->ipL, (size_t)g.n_views * g.n_channels);
+    DEAM_ALLOC(ctx->chan, g.n_channels);
+    DEAM_ALLOC(ctx->row, g.n_rows);
+    DEAM_ALLOC(ctx->slab_views, ctx->n_slabs);
+    DEAM_ALLOC(ctx->dt, (size_t)2 * ctx->nrays);
+    DEAM_ALLOC(ctx->mask, (size_t)ctx->nrays);
+    DEAM_ALLOC(ctx->payload, (size_t)ctx->nrays);
+    DEAM_ALLOC(ctx->volX, volx);
+    DEAM_ALLOC(ctx->volY, voly);
+    DEAM_ALLOC(ctx->partial, (size_t)ctx->n_fwd_blocks);
+    DEAM_ALLOC(ctx->scal, 4);
+    DEAM_ALLOC(ctx->skipped, 1);
+    if (spectra->bowtie) DEAM_ALLOC(ctx->bowtie, g.n_channels);
+    if (ctx->lambda > 0.0) DEAM_ALLOC(ctx->sums, (size_t)ctx->nvox);
+#undef DEAM_ALLOC
     auto A = [&](cudaError_t r) {
         if (e == cudaSuccess) e = r;
     };
-    A(dalloc(&ctx->view4, g.n_views));
-    A(dalloc(&ctx->view_z, g.n_views));
-    A(dalloc(&ctx->ip4, (size_t)g.n_views * g.n_channels));
-    A(dalloc(&ctx->ipL, (size_t)g.n_views * g.n_channels));
-    A(dalloc(&ctx->chan, g.n_channels));
-    A(dalloc(&ctx->row, g.n_rows));
-    A(dalloc(&ctx->slab_views, ctx->n_slabs));
-    A(dalloc(&ctx->dt, (size_t)2 * ctx->nrays));
-    A(dalloc(&ctx->mask, (size_t)ctx->nrays));
-    A(dalloc(&ctx->payload, (size_t)ctx->nrays));
-    A(dalloc(&ctx->volX, volx));
-    A(dalloc(&ctx->volY, voly));
-    A(dalloc(&ctx->partial, (size_t)ctx->n_fwd_blocks));
-    A(dalloc(&ctx->scal, 4));
-    A(dalloc(&ctx->skipped, 1));
-    if (spectra->bowtie) A(dalloc(&ctx->bowtie, g.n_channels));
-    if (ctx->lambda > 0.0) A(dalloc(&ctx->sums, (size_t)ctx->nvox));
     if (e != cudaSuccess) {
         cudaGetLastError();
         free_ctx(ctx);

@@ -237,6 +237,65 @@ def test_host_pointers_to_device_only_arguments_are_rejected(pkg):
     assert gpu.objective(c0.cuda()) > 0          # still usable
 
 
+def test_checkpoint_and_resume_is_bitwise(pkg):
+    # the image is the whole state of an iteration: six iterations in one call
+    # equal three, a copy of the image, and three more
+    case, d, mask, M, c0 = case_data("t3d")
+    gpu = pkg.from_case(case)
+    gpu.set_data(d.cuda())
+    gpu.set_metal_mask(mask.cuda(), "ray")
+    a = c0.clone().cuda()
+    ha = gpu.iterate(a, 6)
+    b = c0.clone().cuda()
+    hb1 = gpu.iterate(b, 3)
+    saved = b.cpu().clone()
+    b2 = saved.cuda()
+    hb2 = gpu.iterate(b2, 3)
+    assert torch.equal(a, b2)
+    np.testing.assert_array_equal(ha, np.concatenate([hb1, hb2]))
+
+
+def test_allocation_failure_is_reported(pkg):
+    # a context whose ray table alone exceeds the device's memory: the first
+    # refused allocation ends deam_init with DEAM_ERR_OOM (no further requests),
+    # and the device stays usable
+    case = synth.make_case("t2d")
+    geo = case.geo.replace(n_views=2_000_000, views_per_rotation=2_000_000, n_channels=10_000,
+                           channel_pitch=1e-4)
+    with pytest.raises(pkg.DeamError) as e:
+        pkg.Deam(geo, case.I0, case.mu)
+    assert e.value.code == pkg.DEAM_ERR_OOM
+    case, d, mask, M, c0 = case_data("t2d")
+    gpu = pkg.from_case(case)
+    gpu.set_data(d.cuda())
+    assert gpu.objective(c0.cuda()) > 0
+
+
+def test_c2_volume_and_detector_at_a_quarter_rotation(pkg):
+    # element-wise parity at the benchmark's volume, detector and spectra
+    # (512x512x64, 16 x 816, 2 x 120 bins, steel hips, noisy counts) with the
+    # view count cut to a quarter rotation (290 views) so that the oracle runs
+    # whole iterations: two iterations, images and objective histories
+    case = synth.make_case("c2s")
+    geo = case.geo.replace(n_views=290)
+    import dataclasses
+    case = dataclasses.replace(case, geo=geo)
+    dev = torch.device("cuda")
+    d, metal = synth.measure(case, device=dev, seed=1)
+    truth, _ = synth.voxelize(case, device=dev)
+    mask = (metal >= case.metal_threshold).to(torch.uint8)
+    c0 = synth.initial_image(case, truth).to(dev)
+    gpu = pkg.from_case(case)
+    gpu.set_data(d)
+    gpu.set_metal_mask(mask, "ray")
+    c = c0.clone()
+    hist = gpu.iterate(c, 2)
+    O = oracle_of(case)
+    c_ref, h_ref, _ = O.iterate(c0.cpu().double().numpy(), d.cpu().double().numpy(), mask.cpu().numpy(), n_iter=2)
+    assert rel_l2(c.cpu().numpy(), c_ref) < 1e-4
+    np.testing.assert_allclose(hist, h_ref, rtol=1e-5)
+
+
 def test_single_voxel_closed_form_on_gpu(pkg):
     # one voxel, one ray, one bin: c' - c* = (1 - mu.L/Z)(c - c*) with Z = (mu1+mu2) L
     geo = synth.Geometry(1, 1, 1, 1, 2.0, 3.0, 4.0, 0.0, 0.0, 0.0, 570.0, 1040.0, 1, 8, 0.0, 0.0, 0.0,
