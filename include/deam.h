@@ -52,7 +52,8 @@ enum {
     DEAM_ERR_CUDA = 2,    /* a CUDA runtime call or kernel failed */
     DEAM_ERR_OOM = 3,     /* device allocation failed */
     DEAM_ERR_STATE = 4,   /* call not valid in the context's state (no data, earlier failure) */
-    DEAM_ERR_TIMEOUT = 5, /* a bounded device wait expired */
+    DEAM_ERR_TIMEOUT = 5, /* a bounded device wait expired (reserved: no kernel here waits on
+                             another block, a flag or a peer, so none is returned) */
     DEAM_ERR_NUMERIC = 6  /* non-finite objective */
 };
 
