@@ -260,8 +260,8 @@ def test_allocation_failure_is_reported(pkg):
     # refused allocation ends deam_init with DEAM_ERR_OOM (no further requests),
     # and the device stays usable
     case = synth.make_case("t2d")
-    geo = case.geo.replace(n_views=2_000_000, views_per_rotation=2_000_000, n_channels=10_000,
-                           channel_pitch=1e-4)
+    geo = case.geo.replace(n_views=2_000_000, views_per_rotation=2_000_000, n_channels=40_000,
+                           channel_pitch=5e-5)   # ray table 1.3 TB
     with pytest.raises(pkg.DeamError) as e:
         pkg.Deam(geo, case.I0, case.mu)
     assert e.value.code == pkg.DEAM_ERR_OOM
