@@ -91,6 +91,30 @@ def test_axis_aligned_ray_through_voxel_centres(oracle_lib):
 @pytest.mark.parametrize("beta,gamma_ch,row,nx,ny", [(0.3, 2, 1, 9, 41), (2.0, -3, 0, 41, 9),
                                                     (4.1, 1, 2, 41, 9), (3.3, 0, 0, 9, 41)])
 def test_partition_of_unity(oracle_lib, beta, gamma_ch, row, nx, ny):
+    _check_partition_of_unity(beta, gamma_ch, row, nx, ny)
+
+
+def test_partition_of_unity_random_rays(oracle_lib):
+    # the same property over random view angles, channels, rows and box shapes
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+
+    @hyp.settings(max_examples=40, deadline=None, derandomize=True)
+    @hyp.given(beta=st.floats(0.0, 2 * math.pi), gamma_ch=st.integers(-3, 3), row=st.integers(0, 2),
+               short=st.integers(5, 11))
+    def check(beta, gamma_ch, row, short):
+        # the box is long across the ray's dominant axis so every sample is interior
+        ang = beta + gamma_ch * 0.002
+        x_dominant = abs(math.cos(ang)) >= abs(math.sin(ang))
+        nx, ny = (short, 41) if x_dominant else (41, short)
+        if abs(abs(math.cos(ang)) - abs(math.sin(ang))) < 0.2:
+            return  # near 45 degrees neither box shape keeps every sample interior
+        _check_partition_of_unity(beta, gamma_ch, row, nx, ny)
+
+    check()
+
+
+def _check_partition_of_unity(beta, gamma_ch, row, nx, ny):
     # For a uniform image every interior sample's weights sum to L, so the line
     # integral of a uniform box is L times the number of planes, i.e. the exact
     # length of the ray between the first and last voxel-centre planes plus one
