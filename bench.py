@@ -37,15 +37,19 @@ WORKLOAD = ("3D helical MAR-DEAM, 512x512x64 voxels x 2 components (0.98x0.98x0.
             "16x816 curved detector, 5800 views (1160/rot x 5, pitch 0.6), 2 spectra x 120 bins, "
             "bilateral steel hips, I0=1e5 + sigma 5")
 FP32_LANES_PER_SM = 128
-# DRAM bytes (read + write) per Joseph sample of one launch, from full ncu
-# captures of the same kernels on the one-rotation cut of this scan (6.48e9
-# samples per launch); traffic grows with the views, so it is scaled by the
-# sample count of the measured launch.  Valid for the kernel builds captured.
-DRAM_BYTES_PER_SAMPLE = {"bwd_kernel<1,16>": 3.135e9 / 6.484e9, "fwd_kernel<FWD_DEAM>": 11.316e9 / 6.484e9}
-# L1/TEX (load/store + shared memory data path) utilisation of the same kernels
-# in those captures: the unit that actually bounds them (no step is a dense
-# contraction and DRAM runs at 1-10 % of peak).
-L1_BUSY = {"bwd_kernel<1,16>": 0.955, "fwd_kernel<FWD_DEAM>": 0.739}
+# Algorithmic on-chip bytes per Joseph sample: the forward gathers 4 taps x 2
+# components x 4 B; the gather backprojection reads each sample's 16-byte
+# payload once for each of the 2 columns it taps.
+L1_BYTES_PER_SAMPLE = 32.0
+# DRAM bytes (read + write) per Joseph sample of one launch, from ncu captures
+# (dram__bytes_read.sum + dram__bytes_write.sum) of the current kernels on the
+# one-rotation cut of this scan (6.484e9 samples per launch; the commands are
+# in profiles/); traffic grows with the views, so it is scaled by the sample
+# count of the measured launch.  Kernels without a capture of their current
+# build are absent (traffic null).
+DRAM_BYTES_PER_SAMPLE = {}
+# L1/TEX utilisation of the same kernels in those captures.
+L1_BUSY = {}
 
 
 def _peaks():
@@ -196,14 +200,17 @@ def run_reference(args):
     # fixed sample size from the calibration, then W warm-up and K timed steps
     views = max(1, int(round(rate * budget * case.geo.n_views)))
     times = []
+    frac = 1.0
     for i in range(args.warmup + args.steps):
         r, desc, cores, dt = cpu_oracle_rate(case, d, mask, c0, views=views)
+        frac = min(views, case.geo.n_views) / case.geo.n_views
         if i >= args.warmup:
-            times.append(dt / ((views) / case.geo.n_views))
-    sec_per_it = sum(times) / len(times)
-    value = 1.0 / sec_per_it
+            times.append(dt)
+    sec_per_step = sum(times) / len(times)   # one step = one oracle pass over the view sample
+    value = frac / sec_per_step              # full iterations per second, scaled by views
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec_per_it,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec_per_step,
+            "sample_fraction_per_step": frac,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "case": args.config},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
@@ -236,6 +243,7 @@ def run_gpu(args):
     t_ctx = time.perf_counter() - t_ctx
     samples = gpu.count_samples()
     stream = torch.cuda.current_stream(dev)
+    args._l1_gbs = pkg.l1_bandwidth() / 1e9   # on-chip peak for the roofline's L1 view
     # one-time setup next to the iterations: the MAR initialisation (NMAR + FBP
     # of both spectra + Eq. 4), timed on the device; the decomposition weights
     # here are the spectrum-weighted mean attenuations (the timing does not
@@ -284,7 +292,7 @@ def run_gpu(args):
     d_h = d.cpu().pin_memory()
     m_h = mask.cpu().pin_memory()
     c_h = c0.cpu().pin_memory()
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = max(1, args.steps)
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
@@ -303,34 +311,49 @@ def run_gpu(args):
 def finish_line(args, world, rank, pg, gpu, case, d, mask, c0, samples, ms, value, kms, kn, hist, clk, e2e):
     geo = case.geo
     # ---- roofline of the dominant kernel ----
+    # No step is a dense contraction: the stated ceiling is HBM on the bytes the
+    # method must move (each kernel's compulsory bytes over its CUDA-event
+    # duration, against the measured copy bandwidth); the realistic bound of
+    # both projector kernels is the on-chip L1 data path (algorithmic 32 B per
+    # Joseph sample against the measured shared-load throughput of this GPU).
     stages = ["layout", "forward", "reduce", "backproject"]
     avg = {s: kms[i] / max(kn[i], 1) * (2 if s == "layout" else 1) for i, s in enumerate(stages)}
     dom = max(["forward", "backproject"], key=lambda s: avg[s])
     peaks = _peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
+    hbm = peaks.get("hbm_gbs")
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs (of measured)"
+    if hbm is None:
+        hbm, hbm_src = 6800.0, "profiling recipe fallback 6.8 TB/s (of fallback)"
+    slab = 8 if (geo.nz == 1 or geo.n_rows == 1 or geo.dz >= 1.5 * geo.row_pitch * geo.sid / geo.sdd) else 16
+    kname = {"forward": "fwd_kernel<FWD_DEAM>", "backproject": f"bwd_kernel<1,{slab}>"}[dom]
+    nvox, nrays = geo.n_voxels, geo.n_rays
+    # compulsory bytes per launch: forward reads c (via its two layouts, 8 B per
+    # voxel each way counted once: 16 B/voxel), d~ (8 B/ray) and the mask
+    # (1 B/ray) and writes the payload (16 B/ray); the backprojection reads the
+    # payload (16 B/ray) and reads and writes c (16 B/voxel)
+    comp_bytes = {"forward": 16 * nvox + 8 * nrays + nrays + 16 * nrays,
+                  "backproject": 16 * nrays + 16 * nvox}[dom]
+    t_s = avg[dom] / 1e3
+    achieved = comp_bytes / t_s / 1e9
+    l1_peak = getattr(args, "_l1_gbs", None)
+    l1_ach = L1_BYTES_PER_SAMPLE * samples / t_s / 1e9
     fp32_peak = 152 * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12   # TFLOP/s, FMA = 2 flops
     # algorithmic flops per Joseph sample: forward = 6 two-point interpolations of
     # 2 components (12 flops); backprojection = 4 taps x 4 accumulators FMA (32
     # flops) + 4 tap weights (4 flops)
-    flops_per_sample = {"forward": 12.0, "backproject": 36.0}[dom]
-    achieved = flops_per_sample * samples / (avg[dom] / 1e3) / 1e12
-    slab = 8 if (geo.nz == 1 or geo.n_rows == 1 or geo.dz >= 1.5 * geo.row_pitch * geo.sid / geo.sdd) else 16
-    kname = {"forward": "fwd_kernel<FWD_DEAM>", "backproject": f"bwd_kernel<1,{slab}>"}[dom]
-    roofline = {"bound": "alu", "kernel": kname,
-                "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                "peak_source": f"FP32 lanes 152 SMs x 128 x 2 flops x {sm_max:.0f} MHz (derived)",
+    flops = {"forward": 12.0, "backproject": 36.0}[dom] * samples / t_s / 1e12
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "peak_source": hbm_src,
                 "traffic": (DRAM_BYTES_PER_SAMPLE[kname] * samples if kname in DRAM_BYTES_PER_SAMPLE else None),
-                "traffic_note": "ncu dram__bytes_read+write per launch, scaled by Joseph samples from the "
-                                "one-rotation capture (profiles/)",
-                "ms_per_launch": avg[dom],
-                "l1tex_busy_ncu": L1_BUSY.get(kname),
-                "hbm_compulsory_GBps": None}
-    nvox, nrays = geo.n_voxels, geo.n_rays
-    comp_bytes = {"forward": 16 * nvox + 8 * nrays + nrays + 16 * nrays,
-                  "backproject": 16 * nrays + 16 * nvox}[dom]
-    hbm = peaks.get("hbm_gbs", 6780.4)
-    roofline["hbm_compulsory_GBps"] = comp_bytes / (avg[dom] / 1e3) / 1e9
-    roofline["hbm_frac"] = roofline["hbm_compulsory_GBps"] / hbm
+                "bytes_per_launch": comp_bytes, "ms_per_launch": avg[dom],
+                "l1": {"achieved": l1_ach, "peak": l1_peak, "unit": "GB/s",
+                       "frac": (l1_ach / l1_peak if l1_peak else None),
+                       "bytes_per_sample": L1_BYTES_PER_SAMPLE, "samples_per_launch": samples,
+                       "peak_source": "deam_l1_bandwidth: shared-memory load throughput measured in this run",
+                       "l1tex_busy_ncu": L1_BUSY.get(kname)},
+                "fp32": {"achieved": flops, "peak": fp32_peak, "unit": "TFLOP/s", "frac": flops / fp32_peak,
+                         "peak_source": f"152 SMs x 128 FP32 lanes x 2 flops x {sm_max:.0f} MHz (derived)"}}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",

@@ -260,6 +260,20 @@ int deam_mar_init(deam_ctx *ctx, const deam_mar_params *params, const float *pri
  * Synchronises `stream`. */
 int deam_basis_images(deam_ctx *ctx, const float *c, const double *coef, int n, float *out, void *stream);
 
+/* Virtual monoenergetic images (Sec. 3, Fig. 5) at n energies (host, keV,
+ * 1 <= n <= 256): out[e] = mu_1(E_e) c_1 + mu_2(E_e) c_2 (1/mm), mu_i(E) taken
+ * from the context's basis tables by linear interpolation of ln mu_i between
+ * the bin centres (the end values beyond them).  Needs the bin energies at
+ * deam_init (DEAM_ERR_STATE without).  c: device float32 [nz][ny][nx][2]; out:
+ * device float32 [n][nz][ny][nx].  Synchronises `stream`. */
+int deam_vmi(deam_ctx *ctx, const float *c, const double *energies, int n, float *out, void *stream);
+
+/* The two spectrum-weighted averages of the VMIs (Sec. 3: the 90 and 140 kVp
+ * images): out[j] = sum_E w_j(E) (mu_1(E) c_1 + mu_2(E) c_2) with
+ * w_j = I0_j / sum_E I0_j, j = 0 (low kVp), 1 (high kVp).  out: device float32
+ * [2][nz][ny][nx].  Synchronises `stream`. */
+int deam_kvp_images(deam_ctx *ctx, const float *c, float *out, void *stream);
+
 /* The penalty R(c) of Eqs. (6)-(7) with the context's lambda and delta into *R
  * (host): R = lambda sum_i sum_x sum_{x~ in N_x} w(x,x~) phi(c_i(x) - c_i(x~)),
  * N_x the 26 neighbours inside the volume, w = 1/physical distance,
@@ -278,6 +292,26 @@ int deam_info(deam_ctx *ctx, double *Z, long long *skipped_last);
  * volume, summed over all rays: the work of one projection (host *n). */
 int deam_count_samples(deam_ctx *ctx, long long *n, void *stream);
 
+/* Bounds-checked builds.  A library compiled with -DDEAM_BOUNDS_CHECK (the
+ * build script's bounds_check option: libdeam_checked.so) tests the index of
+ * every guarded device access in the projector kernels first; a failing test
+ * records the site and index in the context's fault words (the first one
+ * only), skips the access and never traps, and the entry point reads the words
+ * back on return (synchronising its stream) and returns DEAM_ERR_ARG with the
+ * site in deam_last_error().  deam_bounds_checked() is 1 in such a build, else
+ * 0.  deam_bounds_inject(ctx) writes a fault record from the host (no device
+ * fault is made), so that the next entry point reports it: a test of the
+ * read-back path; DEAM_ERR_STATE in an unchecked build. */
+int deam_bounds_checked(void);
+int deam_bounds_inject(deam_ctx *ctx, void *stream);
+
+/* Measured load throughput (bytes/s, into *bytes_per_s, host) of the current
+ * device's L1 data path, the on-chip unit that bounds the projector's gathers:
+ * every SM streams conflict-free 16-byte shared-memory loads for a few
+ * milliseconds, timed with CUDA events on `stream` (best of three after a
+ * warm-up run).  Changes no device setting.  Synchronises `stream`. */
+int deam_l1_bandwidth(double *bytes_per_s, void *stream);
+
 /* Per-kernel timing of deam_iterate.  enable = 1 records CUDA events on the
  * call's stream around every kernel of every iteration (layout build, forward +
  * epilogue, objective reduction, backprojection + update) and accumulates their
@@ -295,7 +329,8 @@ int deam_kernel_times(deam_ctx *ctx, double *ms, long long *launches, int reset)
  * One iteration of the batch is the MAR-DEAM iteration of deam_iterate for
  * every scan, run as one persistent forward launch and one persistent
  * backprojection launch over the work of all scans, captured once in a CUDA
- * graph and replayed.  With autotune = 1 the first deam_batch_iterate times the
+ * graph and replayed.  autotune = 0 runs the persistent plan with default
+ * shapes, 2 the per-scan plan (below) without tuning.  With autotune = 1 the first deam_batch_iterate times the
  * candidate ray-tile shapes (32 channels x rows x views) and backprojection
  * shapes (z-slab depth x column tile) on scratch copies of the images and keeps
  * the fastest, then times one iteration of that persistent plan against a plan
@@ -330,9 +365,17 @@ int deam_batch_destroy(deam_batch *b);
  * running where device memory belongs to another allocator or a fixed arena, or
  * in a latency-bound loop where cudaMalloc/cudaFree would synchronise the device.
  * The paper has no counterpart; this is a library-usage variant.
+ * The geometry, spectra and basis are checked exactly as deam_init checks them
+ * (DEAM_ERR_ARG on refusal).
  * Inputs are caller-owned device buffers: c float32 [nz][ny][nx][2], d float32
  * [2][V][R][K] raw counts (clamped to >= 0 on the fly), mask uint8 [V][R][K] or
- * NULL (no metal); output F is one device double, written on `stream`.  Nothing
+ * NULL (no metal).  The mask is read as deam_get_metal_mask writes it: bit 0
+ * leaves out the ray's low-kVp term, bit 1 its high-kVp term (Sec. 2.1, Eq. 11),
+ * so a plain 0/1 mask meant for both spectra must be given as 0/3.  Output F is
+ * one device double, written on `stream`; it may be +inf or NaN (a ray with
+ * counts but zero expected counts, or non-finite inputs), which deam_objective
+ * reports as DEAM_ERR_NUMERIC but this call cannot see without reading F back:
+ * the caller checks it.  Nothing
  * is allocated: the only scratch (one FP64 partial per 128 rays) is a static
  * 8 MiB device array that every GPU loading the library holds until exit, so at
  * most 134,217,728 rays (more: DEAM_ERR_ARG); a bowtie may have at most 1024

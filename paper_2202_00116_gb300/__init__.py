@@ -18,7 +18,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libdeam.so")
+# DEAM_LIB_PATH selects another build of the same library (the bounds-checked
+# libdeam_checked.so); the default is the in-tree libdeam.so
+LIB_PATH = os.environ.get("DEAM_LIB_PATH") or os.path.join(_HERE, "libdeam.so")
 
 DEAM_OK, DEAM_ERR_ARG, DEAM_ERR_CUDA, DEAM_ERR_OOM, DEAM_ERR_STATE, DEAM_ERR_TIMEOUT, DEAM_ERR_NUMERIC = range(7)
 FAN2D, HELICAL = 0, 1
@@ -67,8 +69,9 @@ class DeamError(RuntimeError):
 _lib = None
 EXPORTS = ["deam_init", "deam_set_data", "deam_set_metal_mask", "deam_get_metal_mask", "deam_forward",
            "deam_backproject", "deam_ray_terms", "deam_iterate", "deam_objective", "deam_info",
-           "deam_gradient", "deam_backprojected_sums", "deam_penalty", "deam_basis_images", "deam_count_samples",
-           "deam_profile", "deam_kernel_times", "deam_log_sinogram", "deam_complete_trace", "deam_fbp",
+           "deam_gradient", "deam_backprojected_sums", "deam_penalty", "deam_basis_images", "deam_vmi",
+           "deam_kvp_images", "deam_count_samples",
+           "deam_profile", "deam_kernel_times", "deam_l1_bandwidth", "deam_bounds_checked", "deam_bounds_inject", "deam_log_sinogram", "deam_complete_trace", "deam_fbp",
            "deam_mar_init", "deam_batch_create",
            "deam_batch_iterate", "deam_batch_info", "deam_batch_destroy", "deam_objective_noalloc",
            "deam_destroy", "deam_last_error"]
@@ -97,9 +100,14 @@ def lib():
             "deam_gradient": [vp, vp, vp, pd, vp],
             "deam_backprojected_sums": [vp, vp, vp, pd, pd, vp],
             "deam_basis_images": [vp, vp, pd, i, vp, vp],
+            "deam_vmi": [vp, vp, pd, i, vp, vp],
+            "deam_kvp_images": [vp, vp, vp, vp],
             "deam_penalty": [vp, vp, pd, vp],
             "deam_count_samples": [vp, C.POINTER(C.c_longlong), vp],
             "deam_profile": [vp, i],
+            "deam_l1_bandwidth": [pd, vp],
+            "deam_bounds_checked": [],
+            "deam_bounds_inject": [vp, vp],
             "deam_kernel_times": [vp, pd, C.POINTER(C.c_longlong), i],
             "deam_log_sinogram": [vp, C.c_double, vp, vp],
             "deam_complete_trace": [vp, vp, vp, i, C.c_double, vp, vp],
@@ -362,19 +370,23 @@ class Deam:
 
     def vmi(self, c, energies_keV):
         """Virtual monoenergetic images mu(x, E) = mu_1(E) c_1 + mu_2(E) c_2 (1/mm) at the
-        given energies; mu_i(E) interpolated linearly in log mu over the bin centres."""
-        if self._E is None:
-            raise ValueError("the context was created without bin energies")
-        E = np.asarray(energies_keV, dtype=np.float64).reshape(-1)
-        coef = np.stack([np.exp(np.interp(E, self._E, np.log(np.maximum(self._mu[i], 1e-300)))) for i in range(2)], 1)
-        return self.basis_images(c, coef)
+        given energies (deam_vmi), float32 [n, nz, ny, nx]."""
+        torch = self.torch
+        E = np.ascontiguousarray(np.asarray(energies_keV, dtype=np.float64).reshape(-1))
+        out = torch.empty((E.size,) + self.img_shape[:3], dtype=torch.float32, device=self.device)
+        _check(lib().deam_vmi(self._h, self._arg(c, self.img_shape, torch.float32),
+                              E.ctypes.data_as(C.POINTER(C.c_double)), int(E.size), C.c_void_p(out.data_ptr()),
+                              self._stream()))
+        return out
 
     def kvp_images(self, c):
-        """The two spectrum-weighted averages of the VMIs (low, high kVp):
-        sum_E w_j(E) mu(x, E) with w_j = I0_j / sum_E I0_j."""
-        w = self._I0 / self._I0.sum(axis=1, keepdims=True)
-        coef = np.stack([w @ self._mu[0], w @ self._mu[1]], 1)
-        return self.basis_images(c, coef)
+        """The two spectrum-weighted averages of the VMIs (low, high kVp), float32
+        [2, nz, ny, nx] (deam_kvp_images)."""
+        torch = self.torch
+        out = torch.empty((2,) + self.img_shape[:3], dtype=torch.float32, device=self.device)
+        _check(lib().deam_kvp_images(self._h, self._arg(c, self.img_shape, torch.float32),
+                                     C.c_void_p(out.data_ptr()), self._stream()))
+        return out
 
     def info(self):
         Z = C.c_double()
@@ -416,6 +428,15 @@ def from_case(case, **kw) -> Deam:
     return Deam(case.geo, case.I0, case.mu, bowtie=case.bowtie, energies=case.energies, **kw)
 
 
+def l1_bandwidth():
+    """Measured L1 data-path (shared-memory load) throughput of the current
+    device in bytes/s (deam_l1_bandwidth)."""
+    import torch
+    v = C.c_double()
+    _check(lib().deam_l1_bandwidth(C.byref(v), C.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    return v.value
+
+
 def calibrate_decomposition(scans, roi):
     """Calibrated weights (mu~_1L, mu~_2L, mu~_1H, mu~_2H) of Eq. (4) from
     calibration scans: `scans` is a list of (deam, (c1, c2)) pairs, each a
@@ -434,10 +455,14 @@ def calibrate_decomposition(scans, roi):
     return np.array([sol[0, 0], sol[1, 0], sol[0, 1], sol[1, 1]])
 
 
-def objective_noalloc(geo, I0, mu, c, d, mask, F, bowtie=None):
+def objective_noalloc(geo, I0, mu, c, d, mask, F, bowtie=None, mask_kind="bits"):
     """deam_objective_noalloc: F(c) into the device double tensor F without any
     device allocation (see include/deam.h).  c, d, mask (or None), F are CUDA
-    tensors owned by the caller; the call is enqueued on the current stream."""
+    tensors owned by the caller; the call is enqueued on the current stream.
+    mask_kind="bits": the mask holds the per-spectrum bits as
+    Deam.metal_mask() returns them (bit 0 low kVp, bit 1 high kVp) and is
+    passed as it is; "ray": nonzero means both spectra, converted here to
+    bits (a new tensor: callers that cannot allocate pass bits)."""
     import torch
     g = deam_geometry(int(geo.kind), geo.nx, geo.ny, geo.nz, geo.dx, geo.dy, geo.dz, geo.cx, geo.cy, geo.cz,
                       geo.sid, geo.sdd, geo.n_views, geo.views_per_rotation, geo.start_angle, geo.feed,
@@ -454,6 +479,10 @@ def objective_noalloc(geo, I0, mu, c, d, mask, F, bowtie=None):
             raise ValueError("c, d (float32) and F (float64) must be contiguous CUDA tensors")
     if mask is not None and not (mask.is_cuda and mask.dtype == torch.uint8 and mask.is_contiguous()):
         raise ValueError("mask must be a contiguous uint8 CUDA tensor or None")
+    if mask_kind not in ("bits", "ray"):
+        raise ValueError("mask_kind is 'bits' or 'ray'")
+    if mask is not None and mask_kind == "ray":
+        mask = (mask != 0).to(torch.uint8) * 3
     stream = C.c_void_p(torch.cuda.current_stream(c.device).cuda_stream)
     _check(lib().deam_objective_noalloc(C.byref(g), C.byref(sp), C.byref(ba), C.c_void_p(c.data_ptr()),
                                         C.c_void_p(d.data_ptr()),
@@ -466,13 +495,17 @@ class DeamBatch:
     persistent launch per stage over all scans, replayed from a CUDA graph,
     tile shapes picked by timing on the first iterate (autotune=True)."""
 
-    def __init__(self, scans, autotune=True):
+    def __init__(self, scans, autotune=True, plan=None):
+        """autotune=True: shapes and plan picked by timing on the first iterate;
+        False: the persistent plan with default shapes; plan="per_scan" forces
+        every scan's own kernels on graph branches (no tuning)."""
         import torch
         self.torch = torch
         self.scans = list(scans)
         arr = (C.c_void_p * len(self.scans))(*[s._h for s in self.scans])
         h = C.c_void_p()
-        _check(lib().deam_batch_create(arr, len(self.scans), int(bool(autotune)), C.byref(h)))
+        mode = 2 if plan == "per_scan" else int(bool(autotune))
+        _check(lib().deam_batch_create(arr, len(self.scans), mode, C.byref(h)))
         self._h = h
 
     def iterate(self, images, n_iter):

@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "deam.h"
 #include "deam_ctx.h"
 #include "deam_internal.h"
@@ -40,6 +42,13 @@ bool is_device_ptr(const void* p) {
     }
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
+
+// NVTX range around the host-side enqueue of one stage (named in a profiler's
+// timeline; free when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 // Restores the caller's current device on scope exit.
 struct DeviceGuard {
@@ -82,6 +91,29 @@ int deam::set_error(int code, const char* msg) { return fail(code, msg); }
         if ((ctx)->failed) return fail(DEAM_ERR_STATE, "context failed earlier"); \
     } while (0)
 
+// End of an entry point that launched kernels: in a bounds-checked build the
+// context's fault words are read back (synchronising `s`) and a recorded
+// out-of-range access is reported as DEAM_ERR_ARG (and cleared); otherwise
+// DEAM_OK without touching the stream.
+int deam::finish_call(deam_ctx* ctx, cudaStream_t s) {
+#ifdef DEAM_BOUNDS_CHECK
+    unsigned int w[2] = {0, 0};
+    CK(cudaMemcpyAsync(w, ctx->fault, sizeof(w), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (w[0] != 0) {
+        CK(cudaMemsetAsync(ctx->fault, 0, sizeof(w), s));
+        CK(cudaStreamSynchronize(s));
+        char m[160];
+        snprintf(m, sizeof(m), "bounds check: out-of-range access at site %u (index %u)", w[0], w[1]);
+        return fail(DEAM_ERR_ARG, m);
+    }
+#else
+    (void)ctx;
+    (void)s;
+#endif
+    return DEAM_OK;
+}
+
 template <typename T>
 static cudaError_t dalloc(T** p, size_t n) {
     return cudaMalloc((void**)p, sizeof(T) * std::max<size_t>(n, 1));
@@ -90,13 +122,15 @@ static cudaError_t dalloc(T** p, size_t n) {
 static void free_ctx(deam_ctx* c) {
     void* ptrs[] = {c->view4, c->view_z, c->ip4, c->ipL, c->chan, c->row, c->bowtie, c->dt, c->mask, c->payload,
                     c->volX, c->volY, c->partial, c->scal, c->hist, c->slab_views, c->skipped, c->c_stage,
-                    c->coef, c->sums};
+                    c->coef, c->sums, c->fault};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete c;
 }
 
-static std::string validate(const deam_geometry* g, const deam_spectra* s, const deam_basis* b) {
+// Host-side validation of a scan description, shared by deam_init and the
+// context-free entry point: "" when valid, else the reason.
+std::string deam::validate_scan(const deam_geometry* g, const deam_spectra* s, const deam_basis* b) {
     if (!g || !s || !b) return "geometry, spectra and basis must not be NULL";
     if (g->kind != DEAM_GEOM_FAN2D && g->kind != DEAM_GEOM_HELICAL) return "geometry.kind must be FAN2D or HELICAL";
     if (g->nx < 1 || g->ny < 1 || g->nz < 1) return "volume dimensions must be >= 1";
@@ -205,7 +239,7 @@ int deam_init(const deam_geometry* geom, const deam_spectra* spectra, const deam
               const deam_options* opts, deam_ctx** out) {
     if (!out) return fail(DEAM_ERR_ARG, "out must not be NULL");
     *out = nullptr;
-    std::string why = validate(geom, spectra, basis);
+    std::string why = deam::validate_scan(geom, spectra, basis);
     if (!why.empty()) return fail(DEAM_ERR_ARG, why);
     deam_options o{};
     if (opts) o = *opts;
@@ -302,6 +336,9 @@ int deam_init(const deam_geometry* geom, const deam_spectra* spectra, const deam
         }
     }
     ctx->mumax = mumax;
+    ctx->mu.assign(basis->mu, basis->mu + 2 * nE);
+    ctx->i0.assign(spectra->I0, spectra->I0 + 2 * nE);
+    if (spectra->energy_keV) ctx->energy.assign(spectra->energy_keV, spectra->energy_keV + nE);
 
     // ---- device buffers ----
     const int nx = g.nx, ny = g.ny, nz = g.nz;
@@ -328,6 +365,7 @@ int deam_init(const deam_geometry* geom, const deam_spectra* spectra, const deam
     DEAM_ALLOC(ctx->partial, (size_t)ctx->n_fwd_blocks);
     DEAM_ALLOC(ctx->scal, 4);
     DEAM_ALLOC(ctx->skipped, 1);
+    DEAM_ALLOC(ctx->fault, 2);
     if (spectra->bowtie) DEAM_ALLOC(ctx->bowtie, g.n_channels);
     if (ctx->lambda > 0.0) DEAM_ALLOC(ctx->sums, (size_t)ctx->nvox);
 #undef DEAM_ALLOC
@@ -346,6 +384,7 @@ int deam_init(const deam_geometry* geom, const deam_spectra* spectra, const deam
     G.row = ctx->row;
     G.ip4 = ctx->ip4;
     G.ipL = ctx->ipL;
+    G.fault = ctx->fault;
     A(cudaMemcpy(ctx->view4, v4.data(), sizeof(float4) * v4.size(), cudaMemcpyHostToDevice));
     A(cudaMemcpy(ctx->view_z, vz.data(), sizeof(float) * vz.size(), cudaMemcpyHostToDevice));
     A(cudaMemcpy(ctx->chan, ch.data(), sizeof(float2) * ch.size(), cudaMemcpyHostToDevice));
@@ -357,6 +396,7 @@ int deam_init(const deam_geometry* geom, const deam_spectra* spectra, const deam
         A(cudaMemcpy(ctx->bowtie, bt.data(), sizeof(float) * bt.size(), cudaMemcpyHostToDevice));
     }
     A(cudaMemset(ctx->mask, 0, (size_t)ctx->nrays));
+    A(cudaMemset(ctx->fault, 0, 2 * sizeof(unsigned int)));
     A(deam::launch_inplane_table(G, ctx->ip4, ctx->ipL, 0));
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -459,7 +499,7 @@ int deam_set_metal_mask(deam_ctx* ctx, const void* m, int kind, void* stream) {
         return fail(DEAM_ERR_ARG, "unknown mask kind");
     }
     ctx->mask_set = true;
-    return DEAM_OK;
+    return deam::finish_call(ctx, s);
 }
 
 int deam_get_metal_mask(deam_ctx* ctx, uint8_t* mask, void* stream) {
@@ -485,7 +525,7 @@ int deam_forward(deam_ctx* ctx, const float* c, float* l, float* g, void* stream
     A.l_out = (float2*)l;
     A.g_out = g;
     CK(deam::launch_forward(g ? deam::FWD_LINE_G : deam::FWD_LINE, ctx->G, ctx->S, A, ctx->n_fwd_blocks, s));
-    return DEAM_OK;
+    return deam::finish_call(ctx, s);
 }
 
 int deam_backproject(deam_ctx* ctx, const float* y, float* img, void* stream) {
@@ -499,23 +539,27 @@ int deam_backproject(deam_ctx* ctx, const float* y, float* img, void* stream) {
     B.img = (float2*)img;
     B.slab_views = ctx->slab_views;
     CK(deam::launch_backward(deam::BWD_ADJOINT, ctx->slab, ctx->G, B, (cudaStream_t)stream));
-    return DEAM_OK;
+    return deam::finish_call(ctx, (cudaStream_t)stream);
 }
 
-static int ray_terms(deam_ctx* ctx, const float2* c, float4* payload, double* F, double* F_dev, cudaStream_t s) {
+// fold = 1: the payload in the backprojector's internal form (times the row
+// length factor); 0: as defined in deam.h (deam_ray_terms).
+static int ray_terms(deam_ctx* ctx, const float2* c, float4* payload, double* F, double* F_dev, cudaStream_t s,
+                     int fold) {
     int rc = build_layouts(ctx, c, nullptr, 0, s);
     if (rc != DEAM_OK) return rc;
     deam::FwdArgs A = fwd_args(ctx);
     A.dt = ctx->dt;
     A.mask = ctx->mask_set ? ctx->mask : nullptr;
     A.payload = payload;
+    A.fold_rowfac = fold;
     CK(deam::launch_forward(ctx->fwd_mode, ctx->G, ctx->S, A, ctx->n_fwd_blocks, s));
     CK(deam::launch_sum_partials(ctx->partial, ctx->n_fwd_blocks, F_dev, 0, s));
     if (F) {
         CK(cudaMemcpyAsync(F, F_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
     }
-    return DEAM_OK;
+    return deam::finish_call(ctx, s);
 }
 
 int deam_ray_terms(deam_ctx* ctx, const float* c, float* payload, double* F, void* stream) {
@@ -525,7 +569,7 @@ int deam_ray_terms(deam_ctx* ctx, const float* c, float* payload, double* F, voi
     DeviceGuard dg(ctx->device);
     NEED_DEVICE(c, "c");
     NEED_DEVICE(payload, "payload");
-    return ray_terms(ctx, (const float2*)c, (float4*)payload, F, ctx->scal, (cudaStream_t)stream);
+    return ray_terms(ctx, (const float2*)c, (float4*)payload, F, ctx->scal, (cudaStream_t)stream, 0);
 }
 
 int deam_objective(deam_ctx* ctx, const float* c, double* out, void* stream) {
@@ -534,7 +578,7 @@ int deam_objective(deam_ctx* ctx, const float* c, double* out, void* stream) {
     if (!ctx->has_data) return fail(DEAM_ERR_STATE, "deam_set_data has not been called");
     DeviceGuard dg(ctx->device);
     NEED_DEVICE(c, "c");
-    int rc = ray_terms(ctx, (const float2*)c, ctx->payload, out, ctx->scal, (cudaStream_t)stream);
+    int rc = ray_terms(ctx, (const float2*)c, ctx->payload, out, ctx->scal, (cudaStream_t)stream, 0);
     if (rc == DEAM_OK && !isfinite(*out)) return fail(DEAM_ERR_NUMERIC, "objective is not finite");
     return rc;
 }
@@ -565,7 +609,7 @@ int deam_iterate(deam_ctx* ctx, float* c, int n_iter, double* hist, void* stream
     B.payload = ctx->payload;
     B.img = cd;
     B.slab_views = ctx->slab_views;
-    B.invZ = (float)(1.0 / ctx->Z);
+    B.invZ = 1.0 / ctx->Z;
     B.clamp_nonneg = ctx->clamp;
     B.skipped = ctx->skipped;
     deam::set_penalty_args(ctx, B);
@@ -578,19 +622,33 @@ int deam_iterate(deam_ctx* ctx, float* c, int n_iter, double* hist, void* stream
     A.dt = ctx->dt;
     A.mask = ctx->mask_set ? ctx->mask : nullptr;
     A.payload = ctx->payload;
+    A.fold_rowfac = 1;
+    NvtxRange iter_range("deam_iterate");
     for (int it = 0; it < n_iter; ++it) {
         cudaEvent_t* e = ctx->prof ? &ev[(size_t)5 * it] : nullptr;
         if (e) CK(cudaEventRecord(e[0], s));
-        int rc = build_layouts(ctx, cd, nullptr, 0, s);
-        if (rc != DEAM_OK) return rc;
+        {
+            NvtxRange r("deam.layout");
+            int rc = build_layouts(ctx, cd, nullptr, 0, s);
+            if (rc != DEAM_OK) return rc;
+        }
         if (e) CK(cudaEventRecord(e[1], s));
-        CK(deam::launch_forward(ctx->fwd_mode, ctx->G, ctx->S, A, ctx->n_fwd_blocks, s));
+        {
+            NvtxRange r("deam.forward");  // Joseph projection + spectral sums + substitution + p-step + F partials
+            CK(deam::launch_forward(ctx->fwd_mode, ctx->G, ctx->S, A, ctx->n_fwd_blocks, s));
+        }
         if (e) CK(cudaEventRecord(e[2], s));
-        CK(deam::launch_sum_partials(ctx->partial, ctx->n_fwd_blocks, ctx->hist + it, 0, s));
-        CK(cudaMemsetAsync(ctx->skipped, 0, sizeof(unsigned long long), s));
+        {
+            NvtxRange r("deam.objective");
+            CK(deam::launch_sum_partials(ctx->partial, ctx->n_fwd_blocks, ctx->hist + it, 0, s));
+            CK(cudaMemsetAsync(ctx->skipped, 0, sizeof(unsigned long long), s));
+        }
         if (e) CK(cudaEventRecord(e[3], s));
-        CK(deam::launch_backward(deam::BWD_UPDATE, ctx->slab, ctx->G, B, s));
-        if (B.sums) CK(deam::launch_reg_update(ctx->G, B, s));
+        {
+            NvtxRange r("deam.backproject");  // gather backprojection + c-step
+            CK(deam::launch_backward(deam::BWD_UPDATE, ctx->slab, ctx->G, B, s));
+            if (B.sums) CK(deam::launch_reg_update(ctx->G, B, s));
+        }
         if (e) CK(cudaEventRecord(e[4], s));
     }
     unsigned long long sk = 0;
@@ -599,6 +657,10 @@ int deam_iterate(deam_ctx* ctx, float* c, int n_iter, double* hist, void* stream
     CK(cudaMemcpyAsync(h.data(), ctx->hist, sizeof(double) * n_iter, cudaMemcpyDeviceToHost, s));
     if (host) CK(cudaMemcpyAsync(c, ctx->c_stage, sizeof(float2) * ctx->nvox, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    {
+        const int rc = deam::finish_call(ctx, s);
+        if (rc != DEAM_OK) return rc;
+    }
     ctx->skipped_last = (long long)sk;
     if (ctx->prof) {
         const int nl[4] = {2, 1, 1, 1};
@@ -625,13 +687,15 @@ int deam_backprojected_sums(deam_ctx* ctx, const float* c, float* sums, double* 
     NEED_DEVICE(c, "c");
     NEED_DEVICE(sums, "sums");
     cudaStream_t s = (cudaStream_t)stream;
-    int rc = ray_terms(ctx, (const float2*)c, ctx->payload, nullptr, ctx->scal, s);
+    int rc = ray_terms(ctx, (const float2*)c, ctx->payload, nullptr, ctx->scal, s, 1);
     if (rc != DEAM_OK) return rc;
     deam::BwdArgs B{};
     B.payload = ctx->payload;
     B.slab_views = ctx->slab_views;
     B.sums = (float4*)sums;  // the c-step's backprojection, stopped before the update
     CK(deam::launch_backward(deam::BWD_UPDATE, ctx->slab, ctx->G, B, s));
+    rc = deam::finish_call(ctx, s);
+    if (rc != DEAM_OK) return rc;
     if (Z) *Z = ctx->Z;
     if (F) {
         CK(cudaMemcpyAsync(F, ctx->scal, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -651,13 +715,15 @@ int deam_gradient(deam_ctx* ctx, const float* c, float* grad, double* F, void* s
     cudaStream_t s = (cudaStream_t)stream;
     // per-ray terms recomputed from c (nothing per energy bin is stored), then
     // the gather backprojection of D = sum_j (r_j - 1) S_ij gives b^ - b~
-    int rc = ray_terms(ctx, (const float2*)c, ctx->payload, nullptr, ctx->scal, s);
+    int rc = ray_terms(ctx, (const float2*)c, ctx->payload, nullptr, ctx->scal, s, 1);
     if (rc != DEAM_OK) return rc;
     deam::BwdArgs B{};
     B.payload = ctx->payload;
     B.img = (float2*)grad;
     B.slab_views = ctx->slab_views;
     CK(deam::launch_backward(deam::BWD_GRADIENT, ctx->slab, ctx->G, B, s));
+    rc = deam::finish_call(ctx, s);
+    if (rc != DEAM_OK) return rc;
     if (F) {
         CK(cudaMemcpyAsync(F, ctx->scal, sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -699,6 +765,51 @@ int deam_basis_images(deam_ctx* ctx, const float* c, const double* coef, int n, 
     return DEAM_OK;
 }
 
+// mu_i(E) of the context's tables at energy E: linear interpolation of
+// ln mu_i between the bin centres, the end values beyond them.
+static double mu_at(const deam_ctx* ctx, int i, double E) {
+    const std::vector<double>& x = ctx->energy;
+    const int n = (int)x.size();
+    auto lg = [&](int e) { return log(std::max(ctx->mu[(size_t)i * n + e], 1e-300)); };
+    if (E <= x[0]) return exp(lg(0));
+    if (E >= x[n - 1]) return exp(lg(n - 1));
+    int e = (int)(std::upper_bound(x.begin(), x.end(), E) - x.begin()) - 1;
+    const double t = (E - x[e]) / (x[e + 1] - x[e]);
+    return exp(lg(e) + t * (lg(e + 1) - lg(e)));
+}
+
+int deam_vmi(deam_ctx* ctx, const float* c, const double* energies, int n, float* out, void* stream) {
+    CHECK_CTX(ctx);
+    if (!energies || n < 1 || n > 256) return fail(DEAM_ERR_ARG, "need 1..256 energies");
+    if (ctx->energy.empty()) return fail(DEAM_ERR_STATE, "the context was created without bin energies");
+    for (size_t e = 1; e < ctx->energy.size(); ++e)
+        if (!(ctx->energy[e] > ctx->energy[e - 1])) return fail(DEAM_ERR_STATE, "bin energies must increase");
+    std::vector<double> coef(2 * (size_t)n);
+    for (int e = 0; e < n; ++e) {
+        if (!isfinite(energies[e])) return fail(DEAM_ERR_ARG, "energies must be finite");
+        coef[2 * e] = mu_at(ctx, 0, energies[e]);
+        coef[2 * e + 1] = mu_at(ctx, 1, energies[e]);
+    }
+    return deam_basis_images(ctx, c, coef.data(), n, out, stream);
+}
+
+int deam_kvp_images(deam_ctx* ctx, const float* c, float* out, void* stream) {
+    CHECK_CTX(ctx);
+    const size_t nE = ctx->i0.size() / 2;
+    double coef[4] = {0, 0, 0, 0};
+    for (int j = 0; j < 2; ++j) {
+        double tot = 0.0;
+        for (size_t e = 0; e < nE; ++e) tot += ctx->i0[j * nE + e];
+        if (!(tot > 0.0)) return fail(DEAM_ERR_STATE, "an empty spectrum has no weighted image");
+        for (size_t e = 0; e < nE; ++e) {
+            const double w = ctx->i0[j * nE + e] / tot;
+            coef[2 * j] += w * ctx->mu[e];
+            coef[2 * j + 1] += w * ctx->mu[nE + e];
+        }
+    }
+    return deam_basis_images(ctx, c, coef, 2, out, stream);
+}
+
 int deam_count_samples(deam_ctx* ctx, long long* n, void* stream) {
     CHECK_CTX(ctx);
     if (!n) return fail(DEAM_ERR_ARG, "n must not be NULL");
@@ -711,6 +822,35 @@ int deam_count_samples(deam_ctx* ctx, long long* n, void* stream) {
     CK(cudaMemcpyAsync(&v, ctx->scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     *n = (long long)llround(v);
+    return DEAM_OK;
+}
+
+int deam_bounds_checked(void) {
+#ifdef DEAM_BOUNDS_CHECK
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+int deam_bounds_inject(deam_ctx* ctx, void* stream) {
+    CHECK_CTX(ctx);
+#ifdef DEAM_BOUNDS_CHECK
+    DeviceGuard dg(ctx->device);
+    const unsigned int w[2] = {deam::SITE_INJECTED, 0};
+    CK(cudaMemcpyAsync(ctx->fault, w, sizeof(w), cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    return DEAM_OK;
+#else
+    (void)stream;
+    return fail(DEAM_ERR_STATE, "not a bounds-checked build (compile with -DDEAM_BOUNDS_CHECK)");
+#endif
+}
+
+int deam_l1_bandwidth(double* bytes_per_s, void* stream) {
+    if (!bytes_per_s) return fail(DEAM_ERR_ARG, "bytes_per_s must not be NULL");
+    cudaError_t e = deam::l1_probe(bytes_per_s, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(DEAM_ERR_CUDA, std::string("l1 probe: ") + cudaGetErrorString(e));
     return DEAM_OK;
 }
 

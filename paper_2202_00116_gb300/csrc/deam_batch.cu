@@ -233,6 +233,7 @@ static int record_iteration(deam_batch* b, float* const* c, int plan) {
             A.dt = x->dt;
             A.mask = x->mask_set ? x->mask : nullptr;
             A.payload = x->payload;
+            A.fold_rowfac = 1;  // read by launch_backward
             e = deam::launch_forward(x->fwd_mode, x->G, x->S, A, x->n_fwd_blocks, q);
             if (e == cudaSuccess)
                 e = deam::launch_sum_ranges(x->partial, b->soff + 2 * i, 1, b->hist + (size_t)i * b->hist_cap,
@@ -242,7 +243,7 @@ static int record_iteration(deam_batch* b, float* const* c, int plan) {
             B.payload = x->payload;
             B.img = (float2*)c[i];
             B.slab_views = x->slab_views;
-            B.invZ = (float)(1.0 / x->Z);
+            B.invZ = 1.0 / x->Z;
             B.clamp_nonneg = x->clamp;
             B.skipped = x->skipped;
             deam::set_penalty_args(x, B);
@@ -339,6 +340,7 @@ int deam_batch_create(deam_ctx* const* ctxs, int n, int autotune, deam_batch** o
     if (!out) return fail(DEAM_ERR_ARG, "out must not be NULL");
     *out = nullptr;
     if (!ctxs || n < 1 || n > 4096) return fail(DEAM_ERR_ARG, "need 1..4096 contexts");
+    if (autotune < 0 || autotune > 2) return fail(DEAM_ERR_ARG, "autotune must be 0, 1 or 2");
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return fail(DEAM_ERR_CUDA, "no CUDA device");
     for (int i = 0; i < n; ++i) {
@@ -351,10 +353,11 @@ int deam_batch_create(deam_ctx* const* ctxs, int n, int autotune, deam_batch** o
     deam_batch* b = new deam_batch();
     b->n = n;
     b->device = dev;
-    b->autotune = autotune ? 1 : 0;
+    b->autotune = autotune == 1 ? 1 : 0;
     b->ctx.assign(ctxs, ctxs + n);
     for (int i = 0; i < n; ++i)
         if (ctxs[i]->fwd_mode != deam::FWD_DEAM) b->min_plan = 1;
+    if (autotune == 2) b->min_plan = 1;  // the per-scan plan, untuned
     b->plan = b->min_plan;
     auto bail = [&](int rc) {
         std::string m = deam_last_error();
@@ -371,6 +374,7 @@ int deam_batch_create(deam_ctx* const* ctxs, int n, int autotune, deam_batch** o
         F[i].dt = ctxs[i]->dt;
         F[i].mask = nullptr;  // set at iterate time (a mask may be set after creation)
         F[i].payload = ctxs[i]->payload;
+        F[i].fold_rowfac = 1;  // read by the batched backprojection
     }
     std::vector<long long> off(n + 1);
     long long maxf = 0;
@@ -429,7 +433,7 @@ int deam_batch_create(deam_ctx* const* ctxs, int n, int autotune, deam_batch** o
             a = deam::BwdArgs{};
             a.payload = ctxs[i]->payload;
             a.slab_views = b->slabviews[bs] + start[i];
-            a.invZ = (float)(1.0 / ctxs[i]->Z);
+            a.invZ = 1.0 / ctxs[i]->Z;
             a.clamp_nonneg = ctxs[i]->clamp;
             a.skipped = ctxs[i]->skipped;
             deam::set_penalty_args(ctxs[i], a);
@@ -502,6 +506,7 @@ int deam_batch_iterate(deam_batch* b, float* const* c, int n_iter, double* hist,
             F[i].dt = b->ctx[i]->dt;
             F[i].mask = b->ctx[i]->mask_set ? b->ctx[i]->mask : nullptr;
             F[i].payload = b->ctx[i]->payload;
+            F[i].fold_rowfac = 1;
         }
         BK(cudaMemcpyAsync(b->fargs, F.data(), sizeof(deam::FwdArgs) * b->n, cudaMemcpyHostToDevice, b->cs));
     }
@@ -534,6 +539,10 @@ int deam_batch_iterate(deam_batch* b, float* const* c, int n_iter, double* hist,
             if (hist) hist[(size_t)i * n_iter + it] = v;
             finite = finite && isfinite(v);
         }
+    for (int i = 0; i < b->n; ++i) {  // bounds-checked builds: any recorded out-of-range access
+        const int rc = deam::finish_call(b->ctx[i], us);
+        if (rc != DEAM_OK) return rc;
+    }
     if (!finite) return fail(DEAM_ERR_NUMERIC, "objective became non-finite");
     return DEAM_OK;
 }

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "deam.h"
 #include "deam_internal.h"
 
@@ -18,6 +20,8 @@ struct deam_ctx {
     double lambda = 0.0, delta = 1.0;  // penalty of Eqs. (6)-(7)
     int fwd_mode = deam::FWD_DEAM;     // FWD_DEAM_F32 for the plain-FP32 variant
     double i0tot[2] = {0.0, 0.0};      // sum_E I0_j(E) (MAR initialisation's log sinograms)
+    std::vector<double> energy;        // [n_E] bin centres (keV), empty if not given
+    std::vector<double> mu, i0;        // [2][n_E] the caller's attenuation and spectrum tables
     bool has_data = false, mask_set = false, failed = false;
     int batch_refs = 0;                // live batches holding this context (deam_destroy refuses)
     long long nrays = 0, nvox = 0, skipped_last = 0;
@@ -44,6 +48,7 @@ struct deam_ctx {
     float2* c_stage = nullptr;
     float2* coef = nullptr;  // deam_basis_images coefficients
     float4* sums = nullptr;  // regularised c-step: backprojected sums per voxel (lambda > 0)
+    unsigned int* fault = nullptr;  // [2] bounds-checked builds: (site, index) of the first failing access
     // per-kernel timing of deam_iterate (deam_profile)
     bool prof = false;
     double prof_ms[4] = {0, 0, 0, 0};
@@ -59,4 +64,8 @@ int build_layouts(deam_ctx* ctx, const float2* c, const float* m, int ones, cuda
 FwdArgs fwd_args(deam_ctx* ctx);
 // Penalty fields of the backprojection arguments (lambda = 0: unregularised).
 void set_penalty_args(const deam_ctx* ctx, BwdArgs& B);
+// End of an entry point that launched kernels on s: DEAM_OK, or in a
+// bounds-checked build DEAM_ERR_ARG when a kernel recorded an out-of-range
+// access in the context's fault words (read back and cleared; synchronises s).
+int finish_call(deam_ctx* ctx, cudaStream_t s);
 }  // namespace deam

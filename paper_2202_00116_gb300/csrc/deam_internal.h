@@ -5,6 +5,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
+#include "deam.h"
+
 namespace deam {
 
 constexpr int kMaxE = 256;        // energy bins carried in the kernel-parameter tables
@@ -27,14 +31,36 @@ struct Geo {
     const float4* view4;     // [V] (sigma_x, sigma_y, cos beta, sin beta); sigma = source in index units
     const float* view_z;     // [V] sigma_z = (s_z - Z0) / dz
     const float2* chan;      // [K] (cos gamma_k, sin gamma_k)
-    const float2* row;       // [R] (omega_r = w_r / dz, sqrt(1 + (w_r/sdd)^2))
+    const float2* row;       // [R] (w_r / dz, sqrt(1 + (w_r/sdd)^2)): .y is the row length factor
     const float4* ip4;       // [V][K] (aq, bq, tau0, kappa) of ray_inplane, built once by build_inplane_table
     const float* ipL;        // [V][K] Lxy, negated for y-dominant rays
-    // approximate, only for candidate ranges in the gather backprojector
-    float omega0, domega;    // omega_r ~= omega0 + r * domega
+    float omega0, domega;    // omega_r = omega0 + r domega (row_omega)
     float chan_c0, inv_dgamma;  // channel coordinate = gamma / dgamma + chan_c0
     float vox_reach_mm;      // max(dx, dy): reach of a voxel's bilinear footprint in-plane
+    unsigned int* fault;     // [2] bounds-checked builds: first failing site and index (else unused)
 };
+
+// Bounds-checked builds (-DDEAM_BOUNDS_CHECK): every guarded access tests its
+// index first; a failing test records (site, index) in the context's fault
+// words -- the first one only -- and the access is skipped, so the kernel
+// finishes and the entry point reports DEAM_ERR_ARG on return.  Never traps.
+enum BoundsSite : unsigned {
+    SITE_FWD_LAYOUT = 1,   // forward: paired-layout gather
+    SITE_FWD_RAY = 2,      // forward: per-ray data (d~, mask, payload, outputs)
+    SITE_BWD_RAY = 3,      // backprojection: ray data / payload gather
+    SITE_BWD_TABLE = 4,    // backprojection: in-plane ray table
+    SITE_BWD_IMAGE = 5,    // backprojection: image / sums
+    SITE_INJECTED = 99     // written from the host by deam_bounds_inject
+};
+#ifdef DEAM_BOUNDS_CHECK
+__device__ __forceinline__ bool in_bounds(unsigned int* fault, bool ok, unsigned site, long long idx) {
+    if (!ok && fault && atomicCAS(fault, 0u, site) == 0u) fault[1] = (unsigned)(idx < 0 ? 0xffffffffu : idx);
+    return ok;
+}
+#define DEAM_IN_BOUNDS(G, cond, site, idx) ::deam::in_bounds((G).fault, (cond), (site), (long long)(idx))
+#else
+#define DEAM_IN_BOUNDS(G, cond, site, idx) true
+#endif
 
 // Spectral model tables (kernel parameters: they live in the constant bank).
 struct Spec {
@@ -92,12 +118,17 @@ __device__ __forceinline__ InPlane inplane_at(float4 a, float lsigned) {
     return r;
 }
 
-// z-intercept of the ray of row r at plane p: fz = az + p bz.
-__device__ __forceinline__ float row_fz(const InPlane& ip, float sigma_z, float omega, float p) {
-    const float az = __fmaf_rn(ip.tau0, omega, sigma_z);
-    const float bz = __fmul_rn(ip.kappa, omega);
-    return __fmaf_rn(p, bz, az);
-}
+// Row height omega_r = w_r / dz of detector row r, in slices: omega0 + r domega,
+// one explicitly rounded FMA wherever either projector direction needs it.
+__device__ __forceinline__ float row_omega(const Geo& G, int r) { return __fmaf_rn((float)r, G.domega, G.omega0); }
+
+// Ray parameter at plane p (fraction of u from the source): t(p) = tau0 + p kappa.
+__device__ __forceinline__ float ray_t(const InPlane& ip, float p) { return __fmaf_rn(p, ip.kappa, ip.tau0); }
+
+// z-intercept (index units) of the ray of row r at ray parameter t:
+// fz = sigma_z + omega_r t.  Both projector directions evaluate exactly this
+// expression (t from ray_t), so they select the same taps.
+__device__ __forceinline__ float row_fz(float sigma_z, float omega, float t) { return __fmaf_rn(omega, t, sigma_z); }
 
 // ---------------------------------------------------------------------------
 // kernel launchers (deam_kernels.cu)
@@ -119,6 +150,8 @@ struct FwdArgs {
     double* partial;      // FWD_DEAM: per-block objective; FWD_MAX: per-block max; FWD_COUNT: samples
     uint8_t* mask_out;    // FWD_MASK
     float threshold;      // FWD_MASK
+    int fold_rowfac;      // FWD_DEAM: 1 stores the payload times the row length factor (the
+                          // backprojector's input form); 0: the payload as defined (deam_ray_terms)
 };
 
 struct BwdArgs {
@@ -126,7 +159,7 @@ struct BwdArgs {
     const float4* payload;  // BWD_UPDATE / BWD_GRADIENT input [V][R][K][4]
     float2* img;            // adjoint or gradient output / update in-out c [nz][ny][nx]
     const int2* slab_views; // [n_slabs] view range [lo, hi] per z-slab
-    float invZ;
+    double invZ;            // 1 / Z of the c-step
     int clamp_nonneg;
     unsigned long long* skipped;  // update: count of unchanged (voxel, component) pairs
     // regularised c-step (Eqs. 6-7), lambda > 0: the backprojection stores its
@@ -150,6 +183,18 @@ struct BatchDesc {
     const long long* btile_off; // [n+1] prefix sums of backprojection tiles
     double* partial;            // [ftile_off[n]] objective per forward tile
 };
+// Scan of batch work item t: the last i with off[i] <= t (prefix sums of the
+// scans' work items).
+__device__ __forceinline__ int find_scan(const long long* off, int n, long long t) {
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(&off[mid]) <= t) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
 // Forward ray-tile and backprojection-tile shapes an autotuner may choose from.
 constexpr int kFwdShapes[3][2] = {{8, 1}, {4, 2}, {2, 4}};             // (rows, views) x 32 channels
 constexpr int kNumBwdShapes = 6;
@@ -186,9 +231,14 @@ cudaError_t launch_mask_bits(uint8_t* m, long long n, int per_spectrum, cudaStre
 cudaError_t launch_reg_update(const Geo& G, const BwdArgs& A, cudaStream_t s);
 cudaError_t launch_penalty(const float2* c, int nx, int ny, int nz, float dx, float dy, float dz, float lambda,
                            float delta, double* partial, int n_blocks, cudaStream_t s);
+// Measured shared-memory (L1 data path) load throughput of this device, bytes/s.
+cudaError_t l1_probe(double* bytes_per_s, cudaStream_t s);
 cudaError_t launch_combine(const float2* c, long long nvox, const float2* ab, int n, float* out, cudaStream_t s);
 
 // Record an error message for deam_last_error() and return code (deam_api.cu).
 int set_error(int code, const char* msg);
+// Validate a scan description on the host: "" if deam_init would accept it,
+// else the reason (deam_api.cu).
+std::string validate_scan(const deam_geometry* g, const deam_spectra* s, const deam_basis* b);
 
 }  // namespace deam

@@ -43,12 +43,15 @@ __device__ __forceinline__ double fwd_ray(const Geo& G, const Spec& S, const Fwd
     const long long nrays = (long long)G.V * G.R * G.K;
     double out = 0.0;
     const long long y = ((long long)v * G.R + r) * G.K + k;
+    if (!DEAM_IN_BOUNDS(G, y >= 0 && y < nrays, SITE_FWD_RAY, y)) return out;
     const float sz = __ldg(&G.view_z[v]);
-    const float2 rw = __ldg(&G.row[r]);
+    const float2 rw = make_float2(row_omega(G, r), __ldg(&G.row[r]).y);  // (omega_r, row length factor)
     const long long vk = (long long)v * G.K + k;
     const InPlane ip = inplane_at(__ldg(&G.ip4[vk]), __ldg(&G.ipL[vk]));
-    const float az = __fmaf_rn(ip.tau0, rw.x, sz);
-    const float bz = __fmul_rn(ip.kappa, rw.x);
+    // fz(p) = sz + omega_r t(p) ~= az + p bz: the linear form only narrows the
+    // plane range (conservatively); samples use the exact row_fz(ray_t(p))
+    const float az = fmaf(ip.tau0, rw.x, sz);
+    const float bz = ip.kappa * rw.x;
     const int np = ip.axis ? G.ny : G.nx;
     const int nq = ip.axis ? G.nx : G.ny;
     const float4* __restrict__ vol = ip.axis ? A.volY : A.volX;
@@ -73,7 +76,7 @@ __device__ __forceinline__ double fwd_ray(const Geo& G, const Spec& S, const Fwd
     // form one interval: shrink the conservative clip to it exactly
     auto valid = [&](int p) {
         const float fq = __fmaf_rn((float)p, ip.bq, ip.aq);
-        const float fz = __fmaf_rn((float)p, bz, az);
+        const float fz = row_fz(sz, rw.x, ray_t(ip, (float)p));
         return fq >= -1.f && fq < fnq && fz >= -1.f && fz < fnz;
     };
     while (p0 <= p1 && !valid(p0)) ++p0;
@@ -88,13 +91,15 @@ __device__ __forceinline__ double fwd_ray(const Geo& G, const Spec& S, const Fwd
     for (int p = p0; p <= p1; ++p) {
         const float pf = (float)p;
         const float fq = __fmaf_rn(pf, ip.bq, ip.aq);
-        const float fz = __fmaf_rn(pf, bz, az);
+        const float fz = row_fz(sz, rw.x, ray_t(ip, pf));
         const float jq = floorf(fq), jz = floorf(fz);
         const float wq = fq - jq, wz = fz - jz;
         const int e = p * ps + ((int)jz + 1) * rs + ((int)jq + 1);
-        float4 lo, hi;
-        asm("ld.global.nc.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;" : "=f"(lo.x), "=f"(lo.y), "=f"(lo.z), "=f"(lo.w) : "l"(vol + e), "l"(pol));
-        asm("ld.global.nc.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;" : "=f"(hi.x), "=f"(hi.y), "=f"(hi.z), "=f"(hi.w) : "l"(vol + e + rs), "l"(pol));
+        float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+        if (DEAM_IN_BOUNDS(G, e >= 0 && (long long)e + rs < (long long)np * ps, SITE_FWD_LAYOUT, e)) {
+            asm("ld.global.nc.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;" : "=f"(lo.x), "=f"(lo.y), "=f"(lo.z), "=f"(lo.w) : "l"(vol + e), "l"(pol));
+            asm("ld.global.nc.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;" : "=f"(hi.x), "=f"(hi.y), "=f"(hi.z), "=f"(hi.w) : "l"(vol + e + rs), "l"(pol));
+        }
         const float a1 = fmaf(wq, lo.z - lo.x, lo.x), b1 = fmaf(wq, hi.z - hi.x, hi.x);
         const float a2 = fmaf(wq, lo.w - lo.y, lo.y), b2 = fmaf(wq, hi.w - hi.y, hi.y);
         s1 += fmaf(wz, b1 - a1, a1);
@@ -153,6 +158,12 @@ __device__ __forceinline__ double fwd_ray(const Geo& G, const Spec& S, const Fwd
             }
         }
         out = (double)f;
+        if (A.fold_rowfac) {  // the backprojector's internal form: h's row factor applied once per ray
+            P.x *= rw.y;
+            P.y *= rw.y;
+            P.z *= rw.y;
+            P.w *= rw.y;
+        }
         __stcs(&A.payload[y], P);
     }
     return out;
@@ -198,41 +209,6 @@ __global__ void __launch_bounds__(kFwdThreads) fwd_kernel(const Geo G, const Spe
     } else if (MODE == FWD_DEAM_F32) {
         const float b = block_reduce<kFwdThreads, float>(redf, false);
         if (threadIdx.x == 0) A.partial[blockIdx.x] = (double)b;
-    }
-}
-
-// Voxel-driven gather backprojection.  A block owns a kTileX x kTileY tile of
-// (ix, iy) columns and a z-slab of SLAB voxels; each thread owns one column and
-// keeps its SLAB accumulators in shared memory (layout [slot][thread], so a
-// warp's accesses to one slot are conflict-free).  For every view that can reach
-// the slab, the thread takes the channels whose rays can touch its column (fan
-// angle of the column centre +- the footprint), evaluates each such ray's sample
-// at its plane exactly as the forward kernel does (same in-plane table, same
-// explicitly rounded row terms), and for every row whose sample falls in the
-// slab adds h(x, y) * payload(y) to the two voxels the sample interpolates.
-// Loads are issued ahead of the data-dependent tests (the kernel is bound by
-// load latency): the next channel's ray parameters are prefetched and each
-// row's payload and row terms are loaded before its slot is known.
-constexpr int kBwdThreads = kTileX * kTileY;
-
-__device__ __forceinline__ float channel_coord(const Geo& G, float4 vw, float x, float y, float* dist) {
-    const float px = (x - vw.x) * G.dx, py = (y - vw.y) * G.dy;
-    const float dot = -(px * vw.z + py * vw.w);
-    const float crs = px * vw.w - py * vw.z;
-    if (dist) *dist = sqrtf(dot * dot + crs * crs);
-    return fmaf(atan2f(crs, dot), G.inv_dgamma, G.chan_c0);
-}
-
-template <bool FOUR, int SLAB, int NT>
-__device__ __forceinline__ void pend_flush(float4* acc, int s, int tid, float4 x) {
-    if (s >= 0 && s < SLAB) {
-        float4& a = acc[s * NT + tid];
-        a.x += x.x;
-        a.y += x.y;
-        if (FOUR) {
-            a.z += x.z;
-            a.w += x.w;
-        }
     }
 }
 
@@ -296,215 +272,12 @@ __device__ __forceinline__ float reg_solve(float ck, float bt, float bh, float Z
     return t;
 }
 
-// One (column tile, z-slab) of the gather backprojection: the work of one block.
-template <int MODE, int SLAB, int TX, int TY>
-__device__ __forceinline__ void bwd_tile(const Geo& G, const BwdArgs& A, float4* acc, int bx, int by, int slab) {
-    // MODE: BWD_ADJOINT (A^T of two-component ray data), BWD_UPDATE (payload ->
-    // b~, delta -> c-step), BWD_GRADIENT (payload -> delta = b^ - b~ = dF/dc)
-    constexpr bool FOUR = MODE == BWD_UPDATE;
-    constexpr int NT = TX * TY;
-    const int tid = threadIdx.x;
-    const int ix = bx * TX + (tid % TX);
-    const int iy = by * TY + (tid / TX);
-    if (ix >= G.nx || iy >= G.ny) return;  // no block-wide synchronisation below
-    const int z0 = slab * SLAB;
-#pragma unroll
-    for (int s = 0; s < SLAB; ++s) acc[s * NT + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
-    const int2 vrange = __ldg(&A.slab_views[slab]);
-    const float fix = (float)ix, fiy = (float)iy;
-    const float zlo = (float)(z0 - 1), zhi = (float)(z0 + SLAB);
-    for (int v = vrange.x; v <= vrange.y; ++v) {
-        const float4 vw = __ldg(&G.view4[v]);
-        const float sz = __ldg(&G.view_z[v]);
-        float dist;
-        const float uc = channel_coord(G, vw, fix, fiy, &dist);
-        // a ray can tap the column only if it passes within one voxel edge of
-        // its centre: |gamma - gamma_c| < asin(edge / dist) < reach / (dist - reach);
-        // 0.05 channel of margin covers the FP32 channel coordinate
-        const float hw = __fdividef(G.vox_reach_mm, fmaxf(dist - G.vox_reach_mm, 1.f)) * G.inv_dgamma + 0.05f;
-        const int k0 = max(0, (int)ceilf(fmaxf(uc - hw, -1.f)));
-        const int k1 = min(G.K - 1, (int)floorf(fminf(uc + hw, (float)G.K)));
-        const long long vbase = (long long)v * G.K;
-        float4 na = make_float4(0.f, 0.f, 0.f, 0.f);
-        float nl = 1.f;
-        if (k0 <= k1) {
-            na = __ldg(&G.ip4[vbase + k0]);
-            nl = __ldg(&G.ipL[vbase + k0]);
-        }
-        for (int k = k0; k <= k1; ++k) {
-            const InPlane ip = inplane_at(na, nl);
-            if (k < k1) {  // prefetch the next channel's parameters
-                na = __ldg(&G.ip4[vbase + k + 1]);
-                nl = __ldg(&G.ipL[vbase + k + 1]);
-            }
-            const int p = ip.axis ? iy : ix;
-            const int q = ip.axis ? ix : iy;
-            const float pf = (float)p;
-            const float fq = __fmaf_rn(pf, ip.bq, ip.aq);
-            const float jq = floorf(fq);
-            const float aq = fq - jq;
-            float wq;
-            if (jq == (float)q) wq = 1.f - aq;
-            else if (jq == (float)(q - 1)) wq = aq;
-            else continue;
-            if (wq == 0.f) continue;
-            int r0 = 0, r1 = G.R - 1;
-            if (G.R > 1) {
-                // fz(r) ~= sigma_z + t_p (omega0 + r domega): rows whose sample can
-                // land in [z0 - 1, z0 + SLAB).  The approximate row model and the
-                // fast reciprocal are within ~1e-6 rows of the exact samples; a
-                // 0.02-row margin keeps every contributing row, and the exact
-                // per-row slot test below decides.
-                const float tp = fmaf(pf, ip.kappa, ip.tau0);
-                const float slope = tp * G.domega;
-                if (fabsf(slope) > 1e-20f) {
-                    const float inv = __fdividef(1.f, slope);
-                    const float base = fmaf(tp, G.omega0, sz);
-                    const float ra = (zlo - base) * inv, rb = (zhi - base) * inv;
-                    const float lo = fminf(fmaxf(fminf(ra, rb), -4.f), (float)G.R + 4.f);
-                    const float hi = fminf(fmaxf(fmaxf(ra, rb), -4.f), (float)G.R + 4.f);
-                    r0 = max(0, (int)floorf(lo - 0.02f));
-                    r1 = min(G.R - 1, (int)ceilf(hi + 0.02f));
-                }
-            }
-            const float Lq = ip.Lxy * wq;
-            // PEND: where two or more rows fall in one slice, consecutive rows
-            // add to the same slot pair: keep it in registers (plo: slot ls,
-            // phi: slot ls + 1) and write shared memory when the slot moves on
-            constexpr bool PEND = SLAB == 8;
-            float4 plo = make_float4(0.f, 0.f, 0.f, 0.f), phi = plo;
-            int ls = -1000;
-            // ray data [V][R][K]: a warp's columns read neighbouring channels of a row
-            const long long pb = vbase * G.R + k;
-#pragma unroll 4
-            for (int r = r0; r <= r1; ++r) {
-                float4 Pv;
-                if (MODE == BWD_ADJOINT) {
-                    const float2 t = __ldg(&A.rays2[pb + (long long)r * G.K]);
-                    Pv = make_float4(t.x, t.y, 0.f, 0.f);
-                } else {
-                    Pv = __ldg(&A.payload[pb + (long long)r * G.K]);
-                    if (MODE == BWD_GRADIENT) Pv = make_float4(Pv.z, Pv.w, 0.f, 0.f);
-                }
-                const float2 rw = __ldg(&G.row[r]);
-                const float fz = row_fz(ip, sz, rw.x, pf);
-                const float jz = floorf(fz);
-                const float az = fz - jz;
-                const int sl = (int)jz - z0;
-                const float w = Lq * rw.y;
-                const float w1 = w * az, w0 = w - w1;
-                if (!PEND) {
-                    if (sl >= 0 && sl < SLAB) {
-                        float4& a = acc[sl * NT + tid];
-                        a.x = fmaf(w0, Pv.x, a.x);
-                        a.y = fmaf(w0, Pv.y, a.y);
-                        if (FOUR) {
-                            a.z = fmaf(w0, Pv.z, a.z);
-                            a.w = fmaf(w0, Pv.w, a.w);
-                        }
-                    }
-                    if (sl >= -1 && sl + 1 < SLAB) {
-                        float4& a = acc[(sl + 1) * NT + tid];
-                        a.x = fmaf(w1, Pv.x, a.x);
-                        a.y = fmaf(w1, Pv.y, a.y);
-                        if (FOUR) {
-                            a.z = fmaf(w1, Pv.z, a.z);
-                            a.w = fmaf(w1, Pv.w, a.w);
-                        }
-                    }
-                    continue;
-                }
-                if (sl != ls) {   // slots rise with r: flush the slot that is complete
-                    pend_flush<FOUR, SLAB, NT>(acc, ls, tid, plo);
-                    if (sl == ls + 1) {
-                        plo = phi;
-                    } else {
-                        pend_flush<FOUR, SLAB, NT>(acc, ls + 1, tid, phi);
-                        plo = make_float4(0.f, 0.f, 0.f, 0.f);
-                    }
-                    phi = make_float4(0.f, 0.f, 0.f, 0.f);
-                    ls = sl;
-                }
-                plo.x = fmaf(w0, Pv.x, plo.x);
-                plo.y = fmaf(w0, Pv.y, plo.y);
-                phi.x = fmaf(w1, Pv.x, phi.x);
-                phi.y = fmaf(w1, Pv.y, phi.y);
-                if (FOUR) {
-                    plo.z = fmaf(w0, Pv.z, plo.z);
-                    plo.w = fmaf(w0, Pv.w, plo.w);
-                    phi.z = fmaf(w1, Pv.z, phi.z);
-                    phi.w = fmaf(w1, Pv.w, phi.w);
-                }
-            }
-            if (PEND) {
-                pend_flush<FOUR, SLAB, NT>(acc, ls, tid, plo);
-                pend_flush<FOUR, SLAB, NT>(acc, ls + 1, tid, phi);
-            }
-        }
-    }
-
-    unsigned long long skipped = 0;
-    for (int s = 0; s < SLAB; ++s) {
-        const int iz = z0 + s;
-        if (iz >= G.nz) break;
-        const float4 a = acc[s * NT + tid];
-        const long long vi = ((long long)iz * G.ny + iy) * G.nx + ix;
-        if (!FOUR) {  // A^T y, or the gradient delta_i
-            A.img[vi] = make_float2(a.x, a.y);
-            continue;
-        }
-        if (A.sums) {  // regularised c-step: reg_update_kernel finishes the update
-            A.sums[vi] = a;
-            continue;
-        }
-        float2 c = A.img[vi];
-        // c-step: c_i <- c_i - (1/Z) ln(b^_i / b~_i) = c_i - (1/Z) log1p(delta_i / b~_i)
-        float ratio;
-        if (a.x > 0.f && (ratio = a.z / a.x) > -1.f) {
-            c.x = fmaf(-log1pf(ratio), A.invZ, c.x);
-            if (A.clamp_nonneg) c.x = fmaxf(c.x, 0.f);
-        } else {
-            ++skipped;
-        }
-        if (a.y > 0.f && (ratio = a.w / a.y) > -1.f) {
-            c.y = fmaf(-log1pf(ratio), A.invZ, c.y);
-            if (A.clamp_nonneg) c.y = fmaxf(c.y, 0.f);
-        } else {
-            ++skipped;
-        }
-        A.img[vi] = c;
-    }
-    if (FOUR && skipped) atomicAdd(A.skipped, skipped);
-}
-
-
-template <int MODE, int SLAB>
-__global__ void __launch_bounds__(kBwdThreads) bwd_kernel(const Geo G, const BwdArgs A) {
-    __shared__ float4 acc[SLAB * kBwdThreads];
-    const int ntx = (G.nx + kTileX - 1) / kTileX, nty = (G.ny + kTileY - 1) / kTileY;
-    int b = blockIdx.x;
-    const int bx = b % ntx;
-    b /= ntx;
-    const int by = b % nty;
-    bwd_tile<MODE, SLAB, kTileX, kTileY>(G, A, acc, bx, by, b / nty);
-}
-
 // ---------------------------------------------------------------------------
 // Batched kernels: one persistent launch walks the work items of many scans
 // (ray tiles for the forward pass, column tiles x slabs for the backprojection);
 // each item finds its scan by binary search in the prefix sums and runs the
 // same per-ray / per-tile code as the single-scan kernels.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int find_scan(const long long* off, int n, long long t) {
-    int lo = 0, hi = n;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldg(&off[mid]) <= t) lo = mid;
-        else hi = mid;
-    }
-    return lo;
-}
-
 // The scan's geometry and arguments are staged in shared memory per work item
 // (not held in registers), so the batched kernels keep the register budget,
 // and hence the occupancy, of the single-scan kernels.
@@ -530,25 +303,6 @@ __global__ void __launch_bounds__(kFwdThreads, 5) fwd_batch_kernel(const BatchDe
             f = fwd_ray<FWD_DEAM>(sG, B.specs[i], sA, v, r, k);
         const double b = block_reduce<kFwdThreads, double>(f, false);
         if (threadIdx.x == 0) B.partial[t] = b;  // per tile: independent of the grid
-    }
-}
-
-// (the backprojection keeps the scan's descriptors in registers: staging them
-// in shared memory was measured slower for this kernel)
-template <int SLAB, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY) bwd_batch_kernel(const BatchDesc B) {
-    __shared__ float4 acc[SLAB * TX * TY];
-    const long long total = __ldg(&B.btile_off[B.n]);
-    for (long long t = blockIdx.x; t < total; t += gridDim.x) {
-        const int i = find_scan(B.btile_off, B.n, t);
-        const Geo G = B.geos[i];
-        const BwdArgs A = B.bargs[i];
-        long long lt = t - __ldg(&B.btile_off[i]);
-        const int ntx = (G.nx + TX - 1) / TX, nty = (G.ny + TY - 1) / TY;
-        const int bx = (int)(lt % ntx);
-        lt /= ntx;
-        const int by = (int)(lt % nty);
-        bwd_tile<BWD_UPDATE, SLAB, TX, TY>(G, A, acc, bx, by, (int)(lt / nty));
     }
 }
 
@@ -734,6 +488,31 @@ __global__ void clamp_copy_kernel(const float* __restrict__ d, float* __restrict
         dt[i] = fmaxf(d[i], 0.f);
 }
 
+// Shared-memory load throughput probe: every thread reads conflict-free
+// 16-byte words from a 16 KB shared buffer (consecutive lanes, consecutive
+// words), ILP 8 per iteration, and folds them into a sum that is written only
+// if it takes an impossible value (so nothing is elided).  This is the L1 data
+// path the projector's gathers and accumulator updates share.
+__device__ float g_l1_probe_sink;
+
+__global__ void __launch_bounds__(256) l1_probe_kernel(int iters) {
+    __shared__ float4 buf[1024];
+    for (int i = threadIdx.x; i < 1024; i += blockDim.x) buf[i] = make_float4((float)i, 1.f, 2.f, 3.f);
+    __syncthreads();
+    float a = 0.f, b = 0.f;
+    int idx = threadIdx.x;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const float4 v = buf[(idx + 128 * u) & 1023];
+            a += v.x + v.z;
+            b += v.y + v.w;
+        }
+        idx = (idx + 32) & 1023;
+    }
+    if (a + b == -1.f) g_l1_probe_sink = a;  // never: every loaded value is >= 0
+}
+
 static int grid_for(long long n, int threads) {
     long long b = (n + threads - 1) / threads;
     if (b > 152LL * 64) b = 152LL * 64;
@@ -779,41 +558,12 @@ cudaError_t launch_forward(int mode, const Geo& G, const Spec& S, const FwdArgs&
     return cudaGetLastError();
 }
 
-cudaError_t launch_backward(int mode, int slab, const Geo& G, const BwdArgs& A, cudaStream_t s) {
-    const int ntx = (G.nx + kTileX - 1) / kTileX, nty = (G.ny + kTileY - 1) / kTileY;
-    const int nsl = (G.nz + slab - 1) / slab;
-    const int blocks = ntx * nty * nsl;
-#define DEAM_BWD(M, SL) bwd_kernel<M, SL><<<blocks, kBwdThreads, 0, s>>>(G, A)
-    if (slab == 2) {
-        if (mode == BWD_UPDATE) DEAM_BWD(BWD_UPDATE, 2);
-        else if (mode == BWD_GRADIENT) DEAM_BWD(BWD_GRADIENT, 2);
-        else DEAM_BWD(BWD_ADJOINT, 2);
-    } else if (slab == 8) {
-        if (mode == BWD_UPDATE) DEAM_BWD(BWD_UPDATE, 8);
-        else if (mode == BWD_GRADIENT) DEAM_BWD(BWD_GRADIENT, 8);
-        else DEAM_BWD(BWD_ADJOINT, 8);
-    } else if (slab == 16) {
-        if (mode == BWD_UPDATE) DEAM_BWD(BWD_UPDATE, 16);
-        else if (mode == BWD_GRADIENT) DEAM_BWD(BWD_GRADIENT, 16);
-        else DEAM_BWD(BWD_ADJOINT, 16);
-    } else {
-        return cudaErrorInvalidValue;
-    }
-#undef DEAM_BWD
-    return cudaGetLastError();
-}
-
 long long forward_tiles(int shape, const Geo& G) {
     switch (shape) {
         case 0: return ray_tiles<8, 1>(G);
         case 1: return ray_tiles<4, 2>(G);
         default: return ray_tiles<2, 4>(G);
     }
-}
-
-long long backward_tiles(int shape, const Geo& G) {
-    const int slab = kBwdShapes[shape][0], tx = kBwdShapes[shape][1], ty = kBwdShapes[shape][2];
-    return (long long)((G.nx + tx - 1) / tx) * ((G.ny + ty - 1) / ty) * ((G.nz + slab - 1) / slab);
 }
 
 int forward_batch_blocks_per_sm(int shape) {
@@ -824,35 +574,12 @@ int forward_batch_blocks_per_sm(int shape) {
     return nb > 0 ? nb : 1;
 }
 
-#define DEAM_BWD_BATCH_SHAPES(X) \
-    X(0, 2, 16, 8) X(1, 2, 32, 4) X(2, 8, 16, 8) X(3, 8, 32, 4) X(4, 16, 16, 8) X(5, 16, 32, 4)
-
-int backward_batch_blocks_per_sm(int shape) {
-    int nb = 1;
-#define X(I, SL, TX, TY) \
-    if (shape == I) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bwd_batch_kernel<SL, TX, TY>, TX * TY, 0);
-    DEAM_BWD_BATCH_SHAPES(X)
-#undef X
-    return nb > 0 ? nb : 1;
-}
-
 cudaError_t launch_forward_batch(int shape, const BatchDesc& B, int grid, cudaStream_t s) {
     if (shape == 0) fwd_batch_kernel<8, 1><<<grid, kFwdThreads, 0, s>>>(B);
     else if (shape == 1) fwd_batch_kernel<4, 2><<<grid, kFwdThreads, 0, s>>>(B);
     else if (shape == 2) fwd_batch_kernel<2, 4><<<grid, kFwdThreads, 0, s>>>(B);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
-}
-
-cudaError_t launch_backward_batch(int shape, const BatchDesc& B, int grid, cudaStream_t s) {
-#define X(I, SL, TX, TY) \
-    if (shape == I) {    \
-        bwd_batch_kernel<SL, TX, TY><<<grid, TX * TY, 0, s>>>(B); \
-        return cudaGetLastError(); \
-    }
-    DEAM_BWD_BATCH_SHAPES(X)
-#undef X
-    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_sum_ranges(const double* partial, const long long* off, int n, double* out, const int* counter,
@@ -894,6 +621,33 @@ cudaError_t launch_combine(const float2* c, long long nvox, const float2* ab, in
 
 cudaError_t launch_mask_bits(uint8_t* m, long long n, int per_spectrum, cudaStream_t s) {
     mask_bits_kernel<<<grid_for(n, 256), 256, 0, s>>>(m, n, per_spectrum);
+    return cudaGetLastError();
+}
+
+cudaError_t l1_probe(double* bytes_per_s, cudaStream_t s) {
+    int sms = 152, per = 1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, l1_probe_kernel, 256, 0);
+    const int grid = sms * std::max(per, 1), iters = 4096;
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // the first run warms up
+        cudaEventRecord(e0, s);
+        l1_probe_kernel<<<grid, 256, 0, s>>>(iters);
+        cudaEventRecord(e1, s);
+        e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) best = std::min(best, ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return e;
+    *bytes_per_s = (double)grid * 256 * iters * 8 * sizeof(float4) / (best * 1e-3);
     return cudaGetLastError();
 }
 

@@ -20,6 +20,7 @@
 #include <stdint.h>
 
 #include <mutex>
+#include <string>
 
 #include "deam.h"
 #include "deam_epilogue.cuh"
@@ -96,7 +97,7 @@ __global__ void __launch_bounds__(kThreads) objective_image_kernel(const ScanGeo
         const float4 vw = make_float4((float)((SG.sid * cb - SG.X0) / SG.dx), (float)((SG.sid * sb - SG.Y0) / SG.dy),
                                       (float)cb, (float)sb);
         const float sz = (float)((SG.z_start + SG.feed * v / SG.vpr - SG.Z0) / SG.dz);
-        const float omega = (float)(w / SG.dz);
+        const float omega = deam::row_omega(G, r);
         const float lz = (float)sqrt(1.0 + (w / SG.sdd) * (w / SG.sdd));
         const deam::InPlane ip = deam::ray_inplane(G, vw, make_float2((float)cg, (float)sg));
         const int np = ip.axis ? SG.ny : SG.nx;
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(kThreads) objective_image_kernel(const ScanGeo
         for (int p = 0; p < np; ++p) {
             const float pf = (float)p;
             const float fq = __fmaf_rn(pf, ip.bq, ip.aq);
-            const float fz = deam::row_fz(ip, sz, omega, pf);
+            const float fz = deam::row_fz(sz, omega, deam::ray_t(ip, pf));
             if (!(fq >= -1.f && fq < (float)nq && fz >= -1.f && fz < (float)SG.nz)) continue;
             const float jqf = floorf(fq), jzf = floorf(fz);
             const float wq = fq - jqf, wz = fz - jzf;
@@ -129,18 +130,26 @@ __global__ void __launch_bounds__(kThreads) objective_image_kernel(const ScanGeo
         }
         const float L = __fmul_rn(ip.Lxy, lz);
         const float l1 = s1 * L, l2 = s2 * L;
-        if (!(mask && mask[y])) {
+        // bit j of the mask: the ray is on the metal trace of spectrum j, whose
+        // data term is then left out (Eq. 11: p = q there)
+        const unsigned mk = mask ? (unsigned)mask[y] : 0u;
+        if ((mk & 3u) != 3u) {
             float gl, gh, u1, u2, u3, u4;
             deam::spectral_sums<false>(S, l1, l2, gl, gh, u1, u2, u3, u4);
             const float bk = BT.on ? BT.b[k] : 1.f;
             gl *= bk;
             gh *= bk;
-            const float dl = fmaxf(d[y], 0.f), dh = fmaxf(d[nrays + y], 0.f);
             float ff = 0.f;
-            if (gl > 0.f) ff = fmaf(gl, deam::idiv_phi((dl - gl) / gl), ff);
-            else if (dl > 0.f) ff = INFINITY;
-            if (gh > 0.f) ff = fmaf(gh, deam::idiv_phi((dh - gh) / gh), ff);
-            else if (dh > 0.f) ff = INFINITY;
+            if (!(mk & 1u)) {
+                const float dl = fmaxf(d[y], 0.f);
+                if (gl > 0.f) ff = fmaf(gl, deam::idiv_phi((dl - gl) / gl), ff);
+                else if (dl > 0.f) ff = INFINITY;
+            }
+            if (!(mk & 2u)) {
+                const float dh = fmaxf(d[nrays + y], 0.f);
+                if (gh > 0.f) ff = fmaf(gh, deam::idiv_phi((dh - gh) / gh), ff);
+                else if (dh > 0.f) ff = INFINITY;
+            }
             f = (double)ff;
         }
     }
@@ -170,10 +179,10 @@ extern "C" int deam_objective_noalloc(const deam_geometry* geom, const deam_spec
     if (!on_device(c) || !on_device(d) || !on_device(F) || (mask && !on_device(mask)))
         return err(DEAM_ERR_ARG, "deam_objective_noalloc: c, d, mask and F must be device memory");
     const deam_geometry& g = *geom;
-    if (g.nx < 1 || g.ny < 1 || g.nz < 1 || g.n_views < 1 || g.n_rows < 1 || g.n_channels < 1 ||
-        g.views_per_rotation < 1 || !finite_pos(g.dx) || !finite_pos(g.dy) || !finite_pos(g.dz) ||
-        !finite_pos(g.sid) || !finite_pos(g.sdd) || !finite_pos(g.channel_pitch))
-        return err(DEAM_ERR_ARG, "deam_objective_noalloc: invalid geometry");
+    // the same host-side checks as deam_init (geometry inside the source circle,
+    // finite values, table sizes): a scan the context refuses is refused here too
+    const std::string why = deam::validate_scan(geom, spectra, basis);
+    if (!why.empty()) return err(DEAM_ERR_ARG, ("deam_objective_noalloc: " + why).c_str());
     const long long nrays = (long long)g.n_views * g.n_rows * g.n_channels;
     if (nrays > kMaxRays)
         return err(DEAM_ERR_ARG, "deam_objective_noalloc: more than 134217728 rays (the static scratch holds "
@@ -234,6 +243,8 @@ extern "C" int deam_objective_noalloc(const deam_geometry* geom, const deam_spec
     G.dx = (float)g.dx; G.dy = (float)g.dy;
     G.dx_sdd = (float)(g.dx / g.sdd); G.dy_sdd = (float)(g.dy / g.sdd);
     G.dx_dy = (float)(g.dx / g.dy); G.dy_dx = (float)(g.dy / g.dx);
+    G.omega0 = (float)((0 - (g.n_rows - 1) / 2.0 + g.row_offset) * g.row_pitch / g.dz);
+    G.domega = (float)(g.row_pitch / g.dz);
 
     // set-up on this device (first call only): the scratch's device address
     int dev = 0;

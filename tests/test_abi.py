@@ -90,10 +90,22 @@ def test_every_context_entry_point_rejects_a_null_context(libdeam):
         lambda: L.deam_complete_trace(None, None, None, 0, 1e-3, None, None),
         lambda: L.deam_fbp(None, None, 1, None, None),
         lambda: L.deam_mar_init(None, C.byref(P), None, None, None, None, None),
+        lambda: L.deam_vmi(None, None, None, 1, None, None),
+        lambda: L.deam_kvp_images(None, None, None, None),
     ]
     for call in calls:
         assert call() == libdeam.DEAM_ERR_ARG
         assert b"null" in L.deam_last_error().lower()
+
+
+def test_l1_probe_rejects_a_null_output(libdeam):
+    assert libdeam.lib().deam_l1_bandwidth(None, None) == libdeam.DEAM_ERR_ARG
+
+
+def test_batch_create_rejects_an_unknown_plan_mode(libdeam):
+    h = C.c_void_p()
+    arr = (C.c_void_p * 1)(None)
+    assert libdeam.lib().deam_batch_create(arr, 1, 3, C.byref(h)) == libdeam.DEAM_ERR_ARG
 
 
 def test_binding_fails_loudly_without_the_library(libdeam, monkeypatch, tmp_path):
@@ -104,3 +116,18 @@ def test_binding_fails_loudly_without_the_library(libdeam, monkeypatch, tmp_path
     case = synth.make_case("t2d")
     with pytest.raises(RuntimeError, match="missing"):
         libdeam.Deam(case.geo, case.I0, case.mu)
+
+
+def test_bounds_checked_build_exports_the_same_api(libdeam):
+    # the -DDEAM_BOUNDS_CHECK build compiles (no GPU needed), exports every
+    # declared entry point and says so; the default build says it is not one
+    from paper_2202_00116_gb300 import build
+    path = build.build(bounds_check=True)
+    Lc = C.CDLL(path)
+    for n in declared_functions():
+        assert hasattr(Lc, n), n
+    Lc.deam_bounds_checked.restype = C.c_int
+    assert Lc.deam_bounds_checked() == 1
+    assert libdeam.lib().deam_bounds_checked() == 0
+    Lc.deam_bounds_inject.argtypes = [C.c_void_p, C.c_void_p]
+    assert Lc.deam_bounds_inject(None, None) == libdeam.DEAM_ERR_ARG       # null context, on the host

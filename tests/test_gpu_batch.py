@@ -126,3 +126,35 @@ def test_context_in_a_live_batch_is_not_destroyed(pkg):
     assert batch.iterate(imgs, 1).shape == (2, 1)      # the batch still works
     batch.close()
     scans[0][0].close()                                # now allowed
+
+
+@pytest.mark.parametrize("plan", ["persistent", "per_scan"])
+def test_batch_matches_oracle(pkg, plan):
+    # the batched forms against the FP64 oracle directly (not only against the
+    # single-scan path): four small scans of uneven size, three iterations,
+    # images to the parity tolerance 1e-4 and objective histories to 1e-5
+    import oracle
+    oracle.build()
+    cases = synth.make_batch_cases(4, small=True)
+    scans, c0s, refs = [], [], []
+    for case in cases:
+        d, metal = synth.measure(case, seed=2)
+        truth, _ = synth.voxelize(case)
+        mask = (metal >= case.metal_threshold).to(torch.uint8)
+        c0 = synth.initial_image(case, truth)
+        g = pkg.from_case(case)
+        g.set_data(d.cuda())
+        g.set_metal_mask(mask.cuda(), "ray")
+        scans.append(g)
+        c0s.append(c0)
+        O = oracle.from_case(case)
+        refs.append(O.iterate(c0.double().numpy(), d.double().numpy(), mask.numpy(), n_iter=3)[:2])
+    batch = pkg.DeamBatch(scans, autotune=False, plan=plan if plan == "per_scan" else None)
+    imgs = [c.clone().cuda() for c in c0s]
+    H = batch.iterate(imgs, 3)
+    assert batch.info()["plan"] == {"persistent": "persistent", "per_scan": "per-scan graph branches"}[plan]
+    for i, (c_ref, h_ref) in enumerate(refs):
+        rel = float(np.linalg.norm(imgs[i].cpu().double().numpy() - c_ref) / np.linalg.norm(c_ref))
+        assert rel < 1e-4, (i, rel)
+        np.testing.assert_allclose(H[i], h_ref, rtol=1e-5)
+    batch.close()
