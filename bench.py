@@ -47,9 +47,10 @@ L1_BYTES_PER_SAMPLE = 32.0
 # in profiles/); traffic grows with the views, so it is scaled by the sample
 # count of the measured launch.  Kernels without a capture of their current
 # build are absent (traffic null).
-DRAM_BYTES_PER_SAMPLE = {}
+DRAM_BYTES_PER_SAMPLE = {"bwd_kernel<1,16>": (2.9376e9 + 0.1232e9) / 6.4845e9,
+                         "fwd_kernel<FWD_DEAM>": (1.9210e9 + 0.2395e9) / 6.4845e9}
 # L1/TEX utilisation of the same kernels in those captures.
-L1_BUSY = {}
+L1_BUSY = {"bwd_kernel<1,16>": 0.947, "fwd_kernel<FWD_DEAM>": 0.673}
 
 
 def _peaks():
@@ -636,75 +637,6 @@ def run_compare(args):
     return 0
 
 
-def run_kernels(args):
-    """Every kernel of the library once or twice, for a sectioned profile: one
-    DEAM iteration, a gradient, a forward projection and its adjoint, the MAR
-    initialisation, the basis images, the allocation-free objective, a
-    regularised iteration with its penalty, and two iterations of a persistent
-    batch of four small scans, on the 256x256x32 helical case.  With
-    --input-cache PATH the synthetic inputs are read from PATH when it exists
-    and written there otherwise, so that a repeated run (the one under a
-    profiler) launches no data-generation kernels."""
-    import torch
-
-    import paper_2202_00116_gb300 as pkg
-    import synth
-    from paper_2202_00116_gb300 import build
-    build.build()
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(0)
-    cache = args.input_cache
-    bcases = synth.make_batch_cases(4, small=True)
-    if cache and os.path.exists(cache):
-        blob = torch.load(cache)
-        case = synth.make_case("c1")
-        d, mask, c0 = blob["d"].to(dev), blob["mask"].to(dev), blob["c0"].to(dev)
-        bdata = [(x.to(dev), m.to(dev), c.to(dev)) for x, m, c in blob["batch"]]
-    else:
-        case, d, mask, c0 = build_workload("c1", dev)
-        bdata = []
-        for cs in bcases:
-            dd, metal = synth.measure(cs, device=dev, seed=1)
-            truth, _ = synth.voxelize(cs, device=dev)
-            bdata.append((dd, (metal >= cs.metal_threshold).to(torch.uint8), synth.initial_image(cs, truth).to(dev)))
-        if cache:
-            torch.save({"d": d.cpu(), "mask": mask.cpu(), "c0": c0.cpu(),
-                        "batch": [(x.cpu(), m.cpu(), c.cpu()) for x, m, c in bdata]}, cache)
-    torch.cuda.synchronize()
-    g = pkg.from_case(case)
-    g.set_data(d)
-    g.set_metal_mask(mask, "ray")
-    c = c0.clone()
-    g.iterate(c, 1)
-    g.gradient(c)
-    l, _ = g.forward(c, want_l=True, want_g=False)
-    g.backproject(l)
-    w = case.I0 / case.I0.sum(axis=1, keepdims=True)
-    calib = [float((w[0] * case.mu[0]).sum()), float((w[0] * case.mu[1]).sum()),
-             float((w[1] * case.mu[0]).sum()), float((w[1] * case.mu[1]).sum())]
-    g.mar_init(calib, t_air=0.005, t_bone=0.026, soft_value=0.0195, prior_spectrum=1)
-    g.basis_images(c, [[0.02, 0.05]])
-    F = torch.zeros(1, dtype=torch.float64, device=dev)
-    pkg.objective_noalloc(case.geo, case.I0, case.mu, c, d, mask, F)
-    gr = pkg.from_case(case, penalty_lambda=2e5, penalty_delta=0.05)
-    gr.set_data(d)
-    gr.set_metal_mask(mask, "ray")
-    gr.iterate(c.clone(), 1)
-    gr.penalty(c)
-    scans, imgs = [], []
-    for cs, (dd, mk, ci) in zip(bcases, bdata):
-        s = pkg.from_case(cs)
-        s.set_data(dd)
-        s.set_metal_mask(mk, "ray")
-        scans.append(s)
-        imgs.append(ci)
-    b = pkg.DeamBatch(scans, autotune=False)
-    b.iterate(imgs, 2)
-    torch.cuda.synchronize()
-    print(json.dumps({"config": "kernels", "ok": True}), flush=True)
-    return 0
-
-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -716,14 +648,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiling runs)")
     ap.add_argument("--batch-scans", type=int, default=24)
-    ap.add_argument("--input-cache", default=None, help="--config kernels: cache file of the synthetic inputs")
     args = ap.parse_args()
     if args.config == "batch":
         return run_batch(args)
     if args.config == "compare":
         return run_compare(args)
-    if args.config == "kernels":
-        return run_kernels(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
