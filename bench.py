@@ -294,18 +294,25 @@ def run_gpu(args):
     m_h = mask.cpu().pin_memory()
     c_h = c0.cpu().pin_memory()
     e2e_steps = max(1, args.steps)
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
+
+    def e2e_step():
         gpu.set_data(d_h)
         gpu.set_metal_mask(m_h, "ray")
         gpu.iterate(c_h, 1)      # copies c in, iterates, copies c and F out (synchronous)
+
+    e2e_step()                   # untimed: the host path's first call sets up its staging buffer
     barrier()
-    e2e_s = reduce_max(pg, time.perf_counter() - t0, dev)
+    with ClockSampler(local) as clk_e2e:
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            e2e_step()
+        barrier()
+        e2e_s = reduce_max(pg, time.perf_counter() - t0, dev)
     e2e_val = world * e2e_steps / e2e_s
     h2d = d_h.numel() * 4 + m_h.numel() + c_h.numel() * 4
     d2h = c_h.numel() * 4 + 8
-    e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+    e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+           "ms_per_step": 1e3 * e2e_s / e2e_steps, "clocks": clk_e2e.summary()}
     return finish_line(args, world, rank, pg, gpu, case, d, mask, c0, samples, ms, value, kms, kn, hist, clk, e2e)
 
 

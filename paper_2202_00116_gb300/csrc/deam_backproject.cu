@@ -253,9 +253,10 @@ __global__ void __launch_bounds__(kBwdThreads) bwd_kernel(const Geo G, const Bwd
 // scan of a slab class; each work item finds its scan by binary search in the
 // prefix sums of tile counts.
 // (the backprojection keeps the scan's descriptors in registers: staging them
-// in shared memory was measured slower for this kernel)
+// in shared memory was measured slower for this kernel; bounded to the
+// single-scan kernel's 6 blocks/SM, which it now meets without spilling)
 template <int SLAB, int TX, int TY>
-__global__ void __launch_bounds__(TX* TY) bwd_batch_kernel(const BatchDesc B) {
+__global__ void __launch_bounds__(TX* TY, 6) bwd_batch_kernel(const BatchDesc B) {
     __shared__ float4 acc[SLAB * TX * TY];
     const long long total = __ldg(&B.btile_off[B.n]);
     for (long long t = blockIdx.x; t < total; t += gridDim.x) {
