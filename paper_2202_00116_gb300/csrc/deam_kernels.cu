@@ -4,12 +4,12 @@
 //                     sums of Eq. (8) for both spectra, the metal-trace
 //                     substitution (Eq. 11), the p-step ratio (Eqs. 9-10), the
 //                     per-ray c-step payload and the I-divergence (Eq. 5);
-//   * bwd_kernel   -- voxel-driven gather backprojection that recomputes the
-//                     forward weights of every candidate ray (exact transpose,
-//                     no atomics), fused with the c-step log-ratio update;
+//   * the batched persistent forward, the regularised c-step (Eqs. 6-7) and
+//     its penalty, the basis images, the on-chip bandwidth probe;
 //   * layout_kernel, reductions and the data clamp.
+// The gather backprojection and the c-step are in deam_backproject.cu.
 // No step is a dense contraction, so no tensor cores are used: the projector is
-// bound by gather/FMA issue, the rest by HBM.
+// bound by its gathers (L1 data path and load latency), the rest by HBM.
 #include <math.h>
 
 #include <algorithm>
