@@ -76,6 +76,30 @@ def _calib(pkg, case):
     return pkg.calibrate_decomposition(scans, roi)
 
 
+def _calib_oracle(case):
+    """The same Eq. (4) calibration through the oracle's own FBP (ROI means,
+    least squares): the weights both sides use in the oracle comparisons, so
+    that no oracle input comes from the CUDA path."""
+    import oracle
+    geo = case.geo
+    O = oracle.from_case(case)
+    rad = 0.35 * min(geo.nx * geo.dx, geo.ny * geo.dy)
+    x, y, _ = synth.voxel_centres(geo)
+    roi = np.broadcast_to((np.hypot(x.numpy()[None, :], y.numpy()[:, None]) < 0.5 * rad)[None],
+                          (geo.nz, geo.ny, geo.nx))
+    A, b = [], []
+    for c2 in (0.0, 0.3):
+        cal = synth.Case("cal", geo, case.energies, case.I0, case.mu, case.mu_metal,
+                         [synth.Obj("cylinder", (0.0, 0.0, 0.0), (rad, rad, 1e4), 0.0, c1=1.0, c2=c2)],
+                         case.i0_total)
+        dc, _ = synth.measure(cal, seed=0, noiseless=True)
+        p = O.log_sinogram(dc.double().numpy())
+        b.append([float(O.fbp(p[j])[roi].mean()) for j in range(2)])
+        A.append([1.0, c2])
+    sol = np.linalg.lstsq(np.asarray(A), np.asarray(b), rcond=None)[0]
+    return np.array([sol[0, 0], sol[1, 0], sol[0, 1], sol[1, 1]])
+
+
 @pytest.mark.parametrize("name", ["t2d", "t3d"])
 def test_log_sinogram_and_trace_completion(pkg, name):
     import oracle
@@ -89,11 +113,14 @@ def test_log_sinogram_and_trace_completion(pkg, name):
     prior = torch.rand(O.ray_shape, generator=torch.Generator().manual_seed(5)) * 3.0
     prior[0, 0, :3] = 0.0                                   # exercises the eps floor
     for j in range(2):
-        pj = p[j].contiguous()
+        # the same sinogram on both sides, the oracle's own (rounded to FP32 for
+        # the GPU): the completion step alone is compared
+        pj = torch.from_numpy(po[j]).float().contiguous().cuda()
         li = g.complete_trace(pj, j).cpu().numpy()
         nm = g.complete_trace(pj, j, prior_proj=prior.cuda(), eps=1e-3).cpu().numpy()
-        li_o = O.complete_trace(pj.cpu().double().numpy(), bits, j)
-        nm_o = O.complete_trace(pj.cpu().double().numpy(), bits, j, prior_proj=prior.double().numpy(), eps=1e-3)
+        pin = pj.cpu().double().numpy()
+        li_o = O.complete_trace(pin, bits, j)
+        nm_o = O.complete_trace(pin, bits, j, prior_proj=prior.double().numpy(), eps=1e-3)
         off = (bits & (1 << j)) == 0
         assert np.array_equal(li[off], pj.cpu().numpy()[off]) and np.array_equal(nm[off], pj.cpu().numpy()[off])
         assert _rel(li, li_o) < 1e-6 and _rel(nm, nm_o) < 1e-6
@@ -110,12 +137,13 @@ def test_fbp_matches_oracle(pkg, name):
     case, d, mask, _, _ = _case(name)
     g = _gpu(pkg, case, d, mask)
     O = oracle.from_case(case)
-    p = g.log_sinogram()
-    img = g.fbp(p)                                          # both spectra in one launch
+    # the oracle's log sinograms, rounded to FP32, are the input of both FBPs
+    p = torch.from_numpy(O.log_sinogram(d.double().numpy(), 1.0)).float().contiguous()
+    img = g.fbp(p.cuda())                                   # both spectra in one launch
     for j in range(2):
-        ref = O.fbp(p[j].cpu().double().numpy())
+        ref = O.fbp(p[j].double().numpy())
         assert _rel(img[j].cpu().numpy(), ref) < 1e-4, j
-        one = g.fbp(p[j].contiguous())
+        one = g.fbp(p[j].contiguous().cuda())
         assert _rel(one.cpu().numpy(), img[j].cpu().numpy()) < 1e-6
 
 
@@ -125,17 +153,24 @@ def test_mar_init_matches_oracle(pkg, name):
     case, d, mask, truth, M = _case(name)
     g = _gpu(pkg, case, d, mask)
     O = oracle.from_case(case)
-    calib = _calib(pkg, case)
-    c, prior, mu = g.mar_init(calib, **MAR)
+    calib = _calib_oracle(case)
+    # the binding's calibration through the GPU FBP gives the same weights
+    np.testing.assert_allclose(_calib(pkg, case), calib, rtol=1e-3)
     dn = d.double().numpy()
-    co, po, mLo, mHo = O.mar_init(dn, mask.numpy(), calib, prior=prior.cpu().double().numpy(), **MAR)
-    assert np.array_equal(po, prior.cpu().double().numpy())
-    assert _rel(mu[0].cpu().numpy(), mLo) < 1e-4 and _rel(mu[1].cpu().numpy(), mHo) < 1e-4
-    assert _rel(c.cpu().numpy(), co) < 1e-4
-    # the GPU's threshold decisions against the oracle's own prior
+    # the whole initialisation, each side on its own data: the oracle runs its
+    # own pipeline end to end (its own FBP, thresholds and prior), and the GPU
+    # runs the same pipeline with the oracle's prior handed in (the one input
+    # where FP32 and FP64 may classify a voxel differently at a threshold), so
+    # nothing the oracle uses comes from the CUDA path
+    co, po_own, mLo, mHo = O.mar_init(dn, mask.numpy(), calib, **MAR)
+    c_o, prior_o, mu_o = g.mar_init(calib, prior=torch.from_numpy(po_own).float().cuda(), **MAR)
+    assert np.array_equal(prior_o.cpu().double().numpy(), po_own.astype(np.float32).astype(np.float64))
+    assert _rel(mu_o[0].cpu().numpy(), mLo) < 1e-4 and _rel(mu_o[1].cpu().numpy(), mHo) < 1e-4
+    assert _rel(c_o.cpu().numpy(), co) < 1e-4
+    # the GPU's own prior: its threshold decisions against the oracle's
+    c, prior, mu = g.mar_init(calib, **MAR)
     bits = O.mask_bits(mask.numpy())
     f = oracle.smooth_inplane(O.fbp(O.complete_trace(O.log_sinogram(dn)[1], bits, 1)), 1)
-    _, po_own, _, _ = O.mar_init(dn, mask.numpy(), calib, **MAR)
     pg = prior.cpu().double().numpy()
 
     def classes(x):   # 0 air, 1 soft tissue, 2 kept (bone) value
@@ -208,15 +243,17 @@ def test_c2_full_size_sampled(pkg):
     po = O.log_sinogram(d.cpu().double().numpy(), 1.0)
     for j in range(2):
         assert _rel(p[j].cpu().numpy(), po[j]) < 1e-6
-    del po
+    # each later step on both sides from the oracle's own high-kVp sinogram
+    # (rounded to FP32 for the GPU), so no oracle input comes from the GPU
+    ph = torch.from_numpy(po[1]).float().contiguous()
+    del po, p
     bits = O.mask_bits(mask.cpu().numpy())
-    ph = p[1].contiguous()
-    li = g.complete_trace(ph, 1)
-    li_o = O.complete_trace(ph.cpu().double().numpy(), bits, 1)
+    li = g.complete_trace(ph.to(dev), 1)
+    li_o = O.complete_trace(ph.double().numpy(), bits, 1)
     assert _rel(li.cpu().numpy(), li_o) < 1e-6
-    del li_o
     img = g.fbp(li)
-    q = O.ramp_filter(li.cpu().double().numpy())
+    q = O.ramp_filter(li_o)
+    del li_o
     vox = np.sort(np.random.default_rng(5).choice(case.geo.n_voxels, size=2000, replace=False))
     ref = O.fbp_backproject_at(q, vox)
     assert _rel(img.reshape(-1)[torch.from_numpy(vox).to(dev)].cpu().numpy(), ref) < 1e-4
