@@ -527,3 +527,39 @@ def test_basis_images_match_oracle(pkg):
     w = case.I0 / case.I0.sum(1, keepdims=True)
     ref = oracle.basis_images(c0.double().numpy(), np.stack([w @ case.mu[0], w @ case.mu[1]], 1))
     assert kvp.shape == (2,) + tuple(c0.shape[:3]) and rel_l2(kvp, ref) < 1e-6
+
+
+@pytest.mark.parametrize("variant", ["single_row_anisotropic", "odd_rows_offset_centre"])
+def test_helical_edge_geometries_match_oracle(pkg, variant):
+    # helical scans off the beaten path, element-wise against the oracle:
+    # a single detector row over a multi-slice volume with dy != dx (the
+    # backprojector's single-row slab and the anisotropic in-plane ratios), and
+    # an odd row count with a row offset, a volume centre off the axis and
+    # dz below the slice a row covers (16-slice slabs over an 11-slice volume)
+    import dataclasses
+    case = synth.make_case("t3d")
+    g = case.geo
+    if variant == "single_row_anisotropic":
+        geo = g.replace(n_rows=1, dy=g.dx * 1.3, feed=2.0, z_start=-3.0, n_views=200)
+    else:
+        geo = g.replace(n_rows=5, row_offset=0.35, cx=7.0, cy=-4.0, cz=1.5, dz=2.0)
+    case = dataclasses.replace(case, geo=geo)
+    d, metal = synth.measure(case, seed=3)
+    truth, _ = synth.voxelize(case)
+    mask = (metal >= case.metal_threshold).to(torch.uint8)
+    c0 = synth.initial_image(case, truth)
+    gpu = pkg.from_case(case)
+    O = oracle_of(case)
+    keep = ~near_tie(geo)
+    l, _ = gpu.forward(c0.cuda())
+    lo = O.forward(c0.double().numpy())
+    assert rel_l2(l.cpu().double().numpy()[keep], lo[keep]) < 1e-5
+    y = synth.random_rays(geo, 4).float()
+    assert rel_l2(gpu.backproject(y.cuda()).cpu().double().numpy(), O.adjoint(y.double().numpy())) < 1e-5
+    gpu.set_data(d.cuda())
+    gpu.set_metal_mask(mask.cuda(), "ray")
+    c = c0.clone().cuda()
+    hist = gpu.iterate(c, 5)
+    c_ref, h_ref, _ = O.iterate(c0.double().numpy(), d.double().numpy(), mask.numpy(), n_iter=5)
+    assert rel_l2(c.cpu().numpy(), c_ref) < 1e-4
+    np.testing.assert_allclose(hist, h_ref, rtol=1e-5)
