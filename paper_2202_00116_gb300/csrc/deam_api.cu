@@ -177,16 +177,21 @@ std::string deam::validate_scan(const deam_geometry* g, const deam_spectra* s, c
 }
 
 // View range [lo, hi] whose rays can put a sample into the z-range of slab s
-// (voxel centres +- one slice of interpolation support).
-int2 deam::slab_view_range(const deam_geometry& g, int s, int slab) {
+// (voxel centres +- one slice of interpolation support) at the columns
+// [ix0, ix1] x [iy0, iy1].  A sample tapping those columns lies within one voxel
+// of them, at most rmax from the rotation axis, so its ray parameter t (the
+// fraction of the source-detector distance) is within (sid -+ rmax) / sdd and its
+// height is s_z + t w for the ray's row height w at the detector.
+int2 deam::slab_view_range(const deam_geometry& g, int s, int slab, int ix0, int ix1, int iy0, int iy1) {
     const int z0 = s * slab, z1 = std::min(g.nz, z0 + slab) - 1;
     if (g.feed == 0.0 || g.nz == 1) return make_int2(0, g.n_views - 1);
     const double Z0 = g.cz - (g.nz - 1) / 2.0 * g.dz;
     const double zlo = Z0 + (z0 - 1) * g.dz, zhi = Z0 + (z1 + 1) * g.dz;
+    const double X0 = g.cx - (g.nx - 1) / 2.0 * g.dx, Y0 = g.cy - (g.ny - 1) / 2.0 * g.dy;
     double rmax = 0.0;
-    for (int sx = -1; sx <= 1; sx += 2)
-        for (int sy = -1; sy <= 1; sy += 2) {
-            double x = g.cx + sx * (g.nx + 1) / 2.0 * g.dx, y = g.cy + sy * (g.ny + 1) / 2.0 * g.dy;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+            const double x = X0 + (a ? ix1 + 1 : ix0 - 1) * g.dx, y = Y0 + (b ? iy1 + 1 : iy0 - 1) * g.dy;
             rmax = std::max(rmax, sqrt(x * x + y * y));
         }
     const double t0 = (g.sid - rmax) / g.sdd, t1 = (g.sid + rmax) / g.sdd;
@@ -204,6 +209,18 @@ int2 deam::slab_view_range(const deam_geometry& g, int s, int slab) {
     hi = std::min(hi, (long long)g.n_views - 1);
     if (lo > hi) return make_int2(1, 0);
     return make_int2((int)lo, (int)hi);
+}
+
+std::vector<int2> deam::tile_view_ranges(const deam_geometry& g, int slab, int tx, int ty) {
+    const int ntx = (g.nx + tx - 1) / tx, nty = (g.ny + ty - 1) / ty, ns = (g.nz + slab - 1) / slab;
+    std::vector<int2> v;
+    v.reserve((size_t)ntx * nty * ns);
+    for (int z = 0; z < ns; ++z)
+        for (int by = 0; by < nty; ++by)
+            for (int bx = 0; bx < ntx; ++bx)
+                v.push_back(slab_view_range(g, z, slab, bx * tx, std::min(g.nx, (bx + 1) * tx) - 1, by * ty,
+                                            std::min(g.ny, (by + 1) * ty) - 1));
+    return v;
 }
 
 int deam::build_layouts(deam_ctx* ctx, const float2* c, const float* m, int ones, cudaStream_t s) {
@@ -297,8 +314,8 @@ int deam_init(const deam_geometry* geom, const deam_spectra* spectra, const deam
         const double w = (r - (g.n_rows - 1) / 2.0 + g.row_offset) * g.row_pitch;
         rw[r] = make_float2((float)(w / g.dz), (float)sqrt(1.0 + (w / g.sdd) * (w / g.sdd)));
     }
-    std::vector<int2> sv(ctx->n_slabs);
-    for (int s = 0; s < ctx->n_slabs; ++s) sv[s] = slab_view_range(g, s, ctx->slab);
+    // per (slab, column tile) in the backprojector's block order
+    const std::vector<int2> sv = deam::tile_view_ranges(g, ctx->slab, deam::kTileX, deam::kTileY);
 
     Geo& G = ctx->G;
     G.nx = g.nx; G.ny = g.ny; G.nz = g.nz; G.V = g.n_views; G.R = g.n_rows; G.K = g.n_channels;
@@ -356,7 +373,7 @@ int deam_init(const deam_geometry* geom, const deam_spectra* spectra, const deam
     DEAM_ALLOC(ctx->ipL, (size_t)g.n_views * g.n_channels);
     DEAM_ALLOC(ctx->chan, g.n_channels);
     DEAM_ALLOC(ctx->row, g.n_rows);
-    DEAM_ALLOC(ctx->slab_views, ctx->n_slabs);
+    DEAM_ALLOC(ctx->slab_views, sv.size());
     DEAM_ALLOC(ctx->dt, (size_t)2 * ctx->nrays);
     DEAM_ALLOC(ctx->mask, (size_t)ctx->nrays);
     DEAM_ALLOC(ctx->payload, (size_t)ctx->nrays);

@@ -62,7 +62,9 @@ __device__ __forceinline__ void bwd_tile(const Geo& G, const BwdArgs& A, float4*
     const int z0 = slab * SLAB;
 #pragma unroll
     for (int s = 0; s < SLAB; ++s) acc[s * NT + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
-    const int2 vrange = __ldg(&A.slab_views[slab]);
+    // views that can reach this column tile's slab (host-computed per tile)
+    const int2 vrange =
+        __ldg(&A.slab_views[((long long)slab * ((G.ny + TY - 1) / TY) + by) * ((G.nx + TX - 1) / TX) + bx]);
     const float fix = (float)ix, fiy = (float)iy;
     const float zlo = (float)(z0 - 1), zhi = (float)(z0 + SLAB);
     for (int v = vrange.x; v <= vrange.y; ++v) {

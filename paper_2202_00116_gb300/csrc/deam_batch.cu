@@ -418,8 +418,9 @@ int deam_batch_create(deam_ctx* const* ctxs, int n, int autotune, deam_batch** o
             // a scan's backprojection tiles appear only in its own slab class
             off[i + 1] = off[i] + (cls[i] == cl ? deam::backward_tiles(bs, G[i]) : 0);
             start[i] = sv.size();
-            const int ns = (ctxs[i]->geo.nz + slab - 1) / slab;
-            for (int z = 0; z < ns; ++z) sv.push_back(deam::slab_view_range(ctxs[i]->geo, z, slab));
+            const std::vector<int2> r = deam::tile_view_ranges(ctxs[i]->geo, slab, deam::kBwdShapes[bs][1],
+                                                               deam::kBwdShapes[bs][2]);
+            sv.insert(sv.end(), r.begin(), r.end());
         }
         A(cudaMalloc((void**)&b->boff[bs], sizeof(long long) * (n + 1)));
         A(cudaMalloc((void**)&b->slabviews[bs], sizeof(int2) * sv.size()));

@@ -56,8 +56,12 @@ struct deam_ctx {
 };
 
 namespace deam {
-// View range [lo, hi] whose rays can put a sample into z-slab s of depth slab.
-int2 slab_view_range(const deam_geometry& g, int s, int slab);
+// View range [lo, hi] whose rays can put a sample into z-slab s of depth slab
+// at the columns [ix0, ix1] x [iy0, iy1].
+int2 slab_view_range(const deam_geometry& g, int s, int slab, int ix0, int ix1, int iy0, int iy1);
+// The ranges of every (slab, tx x ty column tile), slab-major then tile rows:
+// the backprojection's work-item order.
+std::vector<int2> tile_view_ranges(const deam_geometry& g, int slab, int tx, int ty);
 // Projector volume layouts of c (or of the metal image m, or of ones).
 int build_layouts(deam_ctx* ctx, const float2* c, const float* m, int ones, cudaStream_t s);
 // Forward-kernel arguments bound to the context's buffers.

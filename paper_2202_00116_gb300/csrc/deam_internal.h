@@ -158,7 +158,7 @@ struct BwdArgs {
     const float2* rays2;    // BWD_ADJOINT input [V][R][K][2]
     const float4* payload;  // BWD_UPDATE / BWD_GRADIENT input [V][R][K][4]
     float2* img;            // adjoint or gradient output / update in-out c [nz][ny][nx]
-    const int2* slab_views; // [n_slabs] view range [lo, hi] per z-slab
+    const int2* slab_views; // [n_slabs][tiles y][tiles x] view range [lo, hi] per z-slab and column tile
     double invZ;            // 1 / Z of the c-step
     int clamp_nonneg;
     unsigned long long* skipped;  // update: count of unchanged (voxel, component) pairs
