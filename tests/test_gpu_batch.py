@@ -2,6 +2,8 @@
 together must give what deam_iterate gives for each scan alone (same per-ray
 code; the backprojection tile shape the autotuner picks may differ from the
 single-scan one, which changes only the FP32 summation grouping)."""
+import dataclasses
+
 import numpy as np
 import pytest
 import torch
@@ -70,6 +72,35 @@ def test_batch_matches_single_scans(pkg, autotune):
         assert _rel(imgs2[i], c) < 2e-6
         np.testing.assert_allclose(H2[i], h, rtol=1e-6)
     batch.close()
+
+
+@pytest.mark.parametrize("plan", ["persistent", "per_scan"])
+def test_batch_spectral_models(pkg, plan):
+    # every scan with its own source spectra (I0 scaled per scan): each work
+    # item of the persistent forward must use its own scan's spectral tables
+    scans = []
+    for i, case in enumerate(synth.make_batch_cases(6, small=True)):
+        case = dataclasses.replace(case, I0=case.I0 * (1.0 + 0.25 * i))
+        d, metal = synth.measure(case, seed=2)
+        truth, _ = synth.voxelize(case)
+        g = pkg.from_case(case)
+        g.set_data(d.cuda())
+        g.set_metal_mask((metal >= case.metal_threshold).to(torch.uint8).cuda(), "ray")
+        scans.append((g, synth.initial_image(case, truth)))
+    ref = []
+    for g, c0 in scans:
+        c = c0.clone().cuda()
+        ref.append((c, g.iterate(c, 2)))
+    batch = pkg.DeamBatch([g for g, _ in scans], autotune=False, plan=plan if plan == "per_scan" else None)
+    imgs = [c0.clone().cuda() for _, c0 in scans]
+    H = batch.iterate(imgs, 2)
+    assert batch.info()["plan"] == {"persistent": "persistent", "per_scan": "per-scan graph branches"}[plan]
+    for i, (c, h) in enumerate(ref):
+        assert _rel(imgs[i], c) < 1e-6, i
+        np.testing.assert_allclose(H[i], h, rtol=1e-7)
+    batch.close()
+    for g, _ in scans:
+        g.close()
 
 
 def test_batch_rejects_bad_input(pkg):
