@@ -80,7 +80,7 @@ __device__ __forceinline__ void spectral_sums(const Spec& S, float l1, float l2,
                                               float& s1l, float& s2l, float& s1h, float& s2h) {
     float cgl = 0.f, cgh = 0.f, c1l = 0.f, c2l = 0.f, c1h = 0.f, c2h = 0.f;
     gl = gh = s1l = s2l = s1h = s2h = 0.f;
-    if (!COMP) {
+    if constexpr (!COMP) {
         for (int e = S.e_lo; e < S.e_hi; ++e) {
             const float ex = ex2_approx(-fmaf(S.mu1l2[e], l1, S.mu2l2[e] * l2));
             const float ql = S.i0l[e] * ex, qh = S.i0h[e] * ex;
@@ -93,34 +93,34 @@ __device__ __forceinline__ void spectral_sums(const Spec& S, float l1, float l2,
                 s2h = fmaf(S.mu2[e], qh, s2h);
             }
         }
-        return;
-    }
-    for (int e0 = S.e_lo; e0 < S.e_hi; e0 += 8) {
-        float pgl = 0.f, pgh = 0.f, p1l = 0.f, p2l = 0.f, p1h = 0.f, p2h = 0.f;
-        const int n = min(8, S.e_hi - e0);
+    } else {
+        for (int e0 = S.e_lo; e0 < S.e_hi; e0 += 8) {
+            float pgl = 0.f, pgh = 0.f, p1l = 0.f, p2l = 0.f, p1h = 0.f, p2h = 0.f;
+            const int n = min(8, S.e_hi - e0);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            if (i < n) {
-                const int e = e0 + i;
-                const float ex = ex2_approx(-fmaf(S.mu1l2[e], l1, S.mu2l2[e] * l2));
-                const float ql = S.i0l[e] * ex, qh = S.i0h[e] * ex;
-                pgl += ql;
-                pgh += qh;
-                if (NEED_S) {
-                    p1l = fmaf(S.mu1[e], ql, p1l);
-                    p2l = fmaf(S.mu2[e], ql, p2l);
-                    p1h = fmaf(S.mu1[e], qh, p1h);
-                    p2h = fmaf(S.mu2[e], qh, p2h);
+            for (int i = 0; i < 8; ++i) {
+                if (i < n) {
+                    const int e = e0 + i;
+                    const float ex = ex2_approx(-fmaf(S.mu1l2[e], l1, S.mu2l2[e] * l2));
+                    const float ql = S.i0l[e] * ex, qh = S.i0h[e] * ex;
+                    pgl += ql;
+                    pgh += qh;
+                    if (NEED_S) {
+                        p1l = fmaf(S.mu1[e], ql, p1l);
+                        p2l = fmaf(S.mu2[e], ql, p2l);
+                        p1h = fmaf(S.mu1[e], qh, p1h);
+                        p2h = fmaf(S.mu2[e], qh, p2h);
+                    }
                 }
             }
-        }
-        kahan_add(gl, cgl, pgl);
-        kahan_add(gh, cgh, pgh);
-        if (NEED_S) {
-            kahan_add(s1l, c1l, p1l);
-            kahan_add(s2l, c2l, p2l);
-            kahan_add(s1h, c1h, p1h);
-            kahan_add(s2h, c2h, p2h);
+            kahan_add(gl, cgl, pgl);
+            kahan_add(gh, cgh, pgh);
+            if (NEED_S) {
+                kahan_add(s1l, c1l, p1l);
+                kahan_add(s2l, c2l, p2l);
+                kahan_add(s1h, c1h, p1h);
+                kahan_add(s2h, c2h, p2h);
+            }
         }
     }
 }
