@@ -19,11 +19,15 @@ namespace deam {
 // at its plane exactly as the forward kernel does (same in-plane table, same
 // explicitly rounded t(p), omega_r and fz), and for every row whose sample falls
 // in the slab adds h(x, y) * payload(y) to the two voxels the sample
-// interpolates.  The next channel's ray parameters are prefetched and each
-// row's payload is loaded before its slot is known.  The kernel is bound by
-// the L1/shared-memory data path (the accumulator read-modify-writes and the
-// payload gathers), so the row loop reads nothing else: omega_r is computed,
-// and the payload already carries h's row length factor.
+// interpolates.  The kernel is bound by the L1/shared-memory data path (the
+// accumulator read-modify-writes and the payload gathers), so the row loop
+// reads nothing else: omega_r is computed, and the payload already carries h's
+// row length factor.  Views are taken in pairs: the samples of one row from
+// two consecutive views lie within a few hundredths of a slice of each other,
+// so they almost always fall in the same slot pair, and one read-modify-write
+// of each slot adds both (half the accumulator traffic).  With 8-slice slabs
+// (several rows per slice) consecutive rows share a slot pair instead, which
+// is kept in registers.
 constexpr int kBwdThreads = kTileX * kTileY;
 
 __device__ __forceinline__ float channel_coord(const Geo& G, float4 vw, float x, float y, float* dist) {
@@ -48,6 +52,161 @@ __device__ __forceinline__ void pend_flush(float4* acc, int s, int tid, float4 x
 }
 
 
+// One ray's visit of a column: what the row loop needs.
+struct ColRay {
+    long long pb;  // ray-data index of row 0: (v R) K + k
+    float sz;      // sigma_z of the view
+    float tp;      // ray parameter at the column's plane
+    float Lq;      // Joseph length x in-plane bilinear weight (0: the ray misses the column)
+    int r0, r1;    // rows whose sample can land in the slab (r0 > r1: none)
+};
+
+// Channel window [k0, k1] of view v for the column at (fix, fiy) (k0 > k1:
+// none), and the view's sigma_z.
+__device__ __forceinline__ void view_window(const Geo& G, int v, float fix, float fiy, int& k0, int& k1, float& sz) {
+    const float4 vw = __ldg(&G.view4[v]);
+    sz = __ldg(&G.view_z[v]);
+    float dist;
+    const float uc = channel_coord(G, vw, fix, fiy, &dist);
+    // a ray can tap the column only if it passes within one voxel edge of its
+    // centre: |gamma - gamma_c| < asin(edge / dist) < reach / (dist - reach);
+    // 0.05 channel of margin covers the FP32 channel coordinate
+    const float hw = __fdividef(G.vox_reach_mm, fmaxf(dist - G.vox_reach_mm, 1.f)) * G.inv_dgamma + 0.05f;
+    k0 = max(0, (int)ceilf(fmaxf(uc - hw, -1.f)));
+    k1 = min(G.K - 1, (int)floorf(fminf(uc + hw, (float)G.K)));
+    const long long vbase = (long long)v * G.K;
+    if (!DEAM_IN_BOUNDS(G, k0 > k1 || (k0 >= 0 && vbase + k1 < (long long)G.V * G.K), SITE_BWD_TABLE, vbase + k1))
+        k1 = k0 - 1;
+}
+
+__device__ __forceinline__ ColRay no_ray() {
+    ColRay c;
+    c.pb = 0;
+    c.sz = 0.f;
+    c.tp = 0.f;
+    c.Lq = 0.f;
+    c.r0 = 0;
+    c.r1 = -1;
+    return c;
+}
+
+// Ray (v, k) at column (ix, iy), from its in-plane table entry (a4, aL): the
+// sample at the column's plane exactly as the forward kernel evaluates it;
+// Lq = 0 when the ray does not touch the column.
+__device__ __forceinline__ ColRay col_ray(const Geo& G, int v, int k, float4 a4, float aL, int ix, int iy, float sz,
+                                          float zlo, float zhi) {
+    ColRay c;
+    c.pb = (long long)v * G.R * G.K + k;
+    c.sz = sz;
+    c.Lq = 0.f;
+    c.tp = 0.f;
+    c.r0 = 0;
+    c.r1 = -1;
+    const InPlane ip = inplane_at(a4, aL);
+    const int p = ip.axis ? iy : ix;
+    const int q = ip.axis ? ix : iy;
+    const float pf = (float)p;
+    const float fq = __fmaf_rn(pf, ip.bq, ip.aq);
+    const float jq = floorf(fq);
+    const float aq = fq - jq;
+    float wq = 0.f;
+    if (jq == (float)q) wq = 1.f - aq;
+    else if (jq == (float)(q - 1)) wq = aq;
+    c.tp = ray_t(ip, pf);
+    if (wq == 0.f) return c;
+    int r0 = 0, r1 = G.R - 1;
+    if (G.R > 1) {
+        const float slope = c.tp * G.domega;
+        if (fabsf(slope) > 1e-20f) {
+            const float inv = __fdividef(1.f, slope);
+            const float base = fmaf(c.tp, G.omega0, sz);
+            const float ra = (zlo - base) * inv, rb = (zhi - base) * inv;
+            const float lo = fminf(fmaxf(fminf(ra, rb), -4.f), (float)G.R + 4.f);
+            const float hi = fminf(fmaxf(fmaxf(ra, rb), -4.f), (float)G.R + 4.f);
+            r0 = max(0, (int)floorf(lo - 0.02f));
+            r1 = min(G.R - 1, (int)ceilf(hi + 0.02f));
+        }
+    }
+    if (!DEAM_IN_BOUNDS(G, c.pb + (long long)(G.R - 1) * G.K < (long long)G.V * G.R * G.K, SITE_BWD_RAY,
+                        c.pb + (long long)(G.R - 1) * G.K))
+        return c;
+    c.Lq = ip.Lxy * wq;
+    c.r0 = r0;
+    c.r1 = r1;
+    return c;
+}
+
+template <int MODE>
+__device__ __forceinline__ float4 ray_payload(const BwdArgs& A, long long i) {
+    if (MODE == BWD_ADJOINT) {
+        const float2 t = __ldg(&A.rays2[i]);
+        return make_float4(t.x, t.y, 0.f, 0.f);
+    }
+    float4 P = __ldg(&A.payload[i]);
+    if (MODE == BWD_GRADIENT) P = make_float4(P.z, P.w, 0.f, 0.f);
+    return P;
+}
+
+template <bool FOUR, int SLAB, int NT>
+__device__ __forceinline__ void slot_add(float4* acc, int s, int tid, float w, const float4& P) {
+    if (s >= 0 && s < SLAB) {
+        float4& a = acc[s * NT + tid];
+        a.x = fmaf(w, P.x, a.x);
+        a.y = fmaf(w, P.y, a.y);
+        if (FOUR) {
+            a.z = fmaf(w, P.z, a.z);
+            a.w = fmaf(w, P.w, a.w);
+        }
+    }
+}
+
+template <bool FOUR, int SLAB, int NT>
+__device__ __forceinline__ void slot_add2(float4* acc, int s, int tid, float wa, const float4& Pa, float wb,
+                                          const float4& Pb) {
+    if (s >= 0 && s < SLAB) {
+        float4& a = acc[s * NT + tid];
+        a.x = fmaf(wb, Pb.x, fmaf(wa, Pa.x, a.x));
+        a.y = fmaf(wb, Pb.y, fmaf(wa, Pa.y, a.y));
+        if (FOUR) {
+            a.z = fmaf(wb, Pb.z, fmaf(wa, Pa.z, a.z));
+            a.w = fmaf(wb, Pb.w, fmaf(wa, Pa.w, a.w));
+        }
+    }
+}
+
+// Rows of two rays of consecutive views at one column.  Their samples of a row
+// lie within a few hundredths of a slice of each other, so they nearly always
+// fall in the same slot pair: one read-modify-write of each slot serves both.
+template <int MODE, int SLAB, int NT>
+__device__ __forceinline__ void rows_pair(const Geo& G, const BwdArgs& A, float4* acc, int tid, int z0,
+                                          const ColRay& a, const ColRay& b) {
+    constexpr bool FOUR = MODE == BWD_UPDATE;
+    const int r0 = min(a.r0, b.r0), r1 = max(a.r1, b.r1);
+#pragma unroll 2
+    for (int r = r0; r <= r1; ++r) {
+        const float4 Pa = ray_payload<MODE>(A, a.pb + (long long)r * G.K);
+        const float4 Pb = ray_payload<MODE>(A, b.pb + (long long)r * G.K);
+        const float om = row_omega(G, r);
+        const float fza = row_fz(a.sz, om, a.tp), fzb = row_fz(b.sz, om, b.tp);
+        const float jza = floorf(fza), jzb = floorf(fzb);
+        const float aza = fza - jza, azb = fzb - jzb;
+        const int sa = (int)jza - z0, sb = (int)jzb - z0;
+        const float rf = MODE == BWD_ADJOINT ? __ldg(&G.row[r]).y : 1.f;
+        const float wa = a.Lq * rf, wb = b.Lq * rf;
+        const float w1a = wa * aza, w0a = wa - w1a;
+        const float w1b = wb * azb, w0b = wb - w1b;
+        if (sa == sb) {
+            slot_add2<FOUR, SLAB, NT>(acc, sa, tid, w0a, Pa, w0b, Pb);
+            slot_add2<FOUR, SLAB, NT>(acc, sa + 1, tid, w1a, Pa, w1b, Pb);
+        } else {
+            slot_add<FOUR, SLAB, NT>(acc, sa, tid, w0a, Pa);
+            slot_add<FOUR, SLAB, NT>(acc, sa + 1, tid, w1a, Pa);
+            slot_add<FOUR, SLAB, NT>(acc, sb, tid, w0b, Pb);
+            slot_add<FOUR, SLAB, NT>(acc, sb + 1, tid, w1b, Pb);
+        }
+    }
+}
+
 // One (column tile, z-slab) of the gather backprojection: the work of one block.
 template <int MODE, int SLAB, int TX, int TY>
 __device__ __forceinline__ void bwd_tile(const Geo& G, const BwdArgs& A, float4* acc, int bx, int by, int slab) {
@@ -67,136 +226,136 @@ __device__ __forceinline__ void bwd_tile(const Geo& G, const BwdArgs& A, float4*
         __ldg(&A.slab_views[((long long)slab * ((G.ny + TY - 1) / TY) + by) * ((G.nx + TX - 1) / TX) + bx]);
     const float fix = (float)ix, fiy = (float)iy;
     const float zlo = (float)(z0 - 1), zhi = (float)(z0 + SLAB);
-    for (int v = vrange.x; v <= vrange.y; ++v) {
-        const float4 vw = __ldg(&G.view4[v]);
-        const float sz = __ldg(&G.view_z[v]);
-        float dist;
-        const float uc = channel_coord(G, vw, fix, fiy, &dist);
-        // a ray can tap the column only if it passes within one voxel edge of
-        // its centre: |gamma - gamma_c| < asin(edge / dist) < reach / (dist - reach);
-        // 0.05 channel of margin covers the FP32 channel coordinate
-        const float hw = __fdividef(G.vox_reach_mm, fmaxf(dist - G.vox_reach_mm, 1.f)) * G.inv_dgamma + 0.05f;
-        const int k0 = max(0, (int)ceilf(fmaxf(uc - hw, -1.f)));
-        int k1 = min(G.K - 1, (int)floorf(fminf(uc + hw, (float)G.K)));
-        const long long vbase = (long long)v * G.K;
-        float4 na = make_float4(0.f, 0.f, 0.f, 0.f);
-        float nl = 1.f;
-        if (!DEAM_IN_BOUNDS(G, k0 > k1 || (k0 >= 0 && vbase + k1 < (long long)G.V * G.K), SITE_BWD_TABLE, vbase + k1))
-            k1 = k0 - 1;
-        if (k0 <= k1) {
-            na = __ldg(&G.ip4[vbase + k0]);
-            nl = __ldg(&G.ipL[vbase + k0]);
+    if constexpr (SLAB != 8) {
+        // views in pairs (v, v + 1): the j-th channel of one with the j-th of the other
+        for (int v = vrange.x; v <= vrange.y; v += 2) {
+            int ka0, ka1, kb0 = 0, kb1 = -1;
+            float sza, szb = 0.f;
+            view_window(G, v, fix, fiy, ka0, ka1, sza);
+            if (v + 1 <= vrange.y) view_window(G, v + 1, fix, fiy, kb0, kb1, szb);
+            const int nj = max(ka1 - ka0, kb1 - kb0) + 1;
+            for (int j = 0; j < nj; ++j) {
+                ColRay a = no_ray(), b = no_ray();
+                if (ka0 + j <= ka1) {
+                    const long long i = (long long)v * G.K + ka0 + j;
+                    a = col_ray(G, v, ka0 + j, __ldg(&G.ip4[i]), __ldg(&G.ipL[i]), ix, iy, sza, zlo, zhi);
+                }
+                if (kb0 + j <= kb1) {
+                    const long long i = (long long)(v + 1) * G.K + kb0 + j;
+                    b = col_ray(G, v + 1, kb0 + j, __ldg(&G.ip4[i]), __ldg(&G.ipL[i]), ix, iy, szb, zlo, zhi);
+                }
+                if (a.Lq == 0.f && b.Lq == 0.f) continue;
+                // a missing partner: the other ray with zero weight (same slots, same loads)
+                if (a.Lq == 0.f) {
+                    a = b;
+                    a.Lq = 0.f;
+                }
+                if (b.Lq == 0.f) {
+                    b = a;
+                    b.Lq = 0.f;
+                }
+                rows_pair<MODE, SLAB, NT>(G, A, acc, tid, z0, a, b);
+            }
         }
-        for (int k = k0; k <= k1; ++k) {
-            const InPlane ip = inplane_at(na, nl);
-            if (k < k1) {  // prefetch the next channel's parameters
-                na = __ldg(&G.ip4[vbase + k + 1]);
-                nl = __ldg(&G.ipL[vbase + k + 1]);
+    } else {
+        for (int v = vrange.x; v <= vrange.y; ++v) {
+            int k0, k1;
+            float sz;
+            view_window(G, v, fix, fiy, k0, k1, sz);
+            const long long vbase = (long long)v * G.K;
+            float4 na = make_float4(0.f, 0.f, 0.f, 0.f);
+            float nl = 1.f;
+            if (k0 <= k1) {
+                na = __ldg(&G.ip4[vbase + k0]);
+                nl = __ldg(&G.ipL[vbase + k0]);
             }
-            const int p = ip.axis ? iy : ix;
-            const int q = ip.axis ? ix : iy;
-            const float pf = (float)p;
-            const float fq = __fmaf_rn(pf, ip.bq, ip.aq);
-            const float jq = floorf(fq);
-            const float aq = fq - jq;
-            float wq;
-            if (jq == (float)q) wq = 1.f - aq;
-            else if (jq == (float)(q - 1)) wq = aq;
-            else continue;
-            if (wq == 0.f) continue;
-            const float tp = ray_t(ip, pf);  // ray parameter at plane p
-            int r0 = 0, r1 = G.R - 1;
-            if (G.R > 1) {
-                // fz(r) = sigma_z + t (omega0 + r domega): rows whose sample can
-                // land in [z0 - 1, z0 + SLAB).  Solved in FP32 with the fast
-                // reciprocal (within ~1e-6 rows of the rounded samples); a
-                // 0.02-row margin keeps every contributing row, and the exact
-                // per-row slot test below decides.
-                const float slope = tp * G.domega;
-                if (fabsf(slope) > 1e-20f) {
-                    const float inv = __fdividef(1.f, slope);
-                    const float base = fmaf(tp, G.omega0, sz);
-                    const float ra = (zlo - base) * inv, rb = (zhi - base) * inv;
-                    const float lo = fminf(fmaxf(fminf(ra, rb), -4.f), (float)G.R + 4.f);
-                    const float hi = fminf(fmaxf(fmaxf(ra, rb), -4.f), (float)G.R + 4.f);
-                    r0 = max(0, (int)floorf(lo - 0.02f));
-                    r1 = min(G.R - 1, (int)ceilf(hi + 0.02f));
+            for (int k = k0; k <= k1; ++k) {
+                const InPlane ip = inplane_at(na, nl);
+                if (k < k1) {  // prefetch the next channel's parameters
+                    na = __ldg(&G.ip4[vbase + k + 1]);
+                    nl = __ldg(&G.ipL[vbase + k + 1]);
                 }
-            }
-            const float Lq = ip.Lxy * wq;
-            // PEND: where two or more rows fall in one slice, consecutive rows
-            // add to the same slot pair: keep it in registers (plo: slot ls,
-            // phi: slot ls + 1) and write shared memory when the slot moves on
-            constexpr bool PEND = SLAB == 8;
-            float4 plo = make_float4(0.f, 0.f, 0.f, 0.f), phi = plo;
-            int ls = -1000;
-            // ray data [V][R][K]: a warp's columns read neighbouring channels of a row
-            const long long pb = vbase * G.R + k;
-            if (!DEAM_IN_BOUNDS(G, pb + (long long)r1 * G.K < (long long)G.V * G.R * G.K, SITE_BWD_RAY,
-                                pb + (long long)r1 * G.K))
-                continue;
-#pragma unroll 4
-            for (int r = r0; r <= r1; ++r) {
-                float4 Pv;
-                if (MODE == BWD_ADJOINT) {
-                    const float2 t = __ldg(&A.rays2[pb + (long long)r * G.K]);
-                    Pv = make_float4(t.x, t.y, 0.f, 0.f);
-                } else {
-                    Pv = __ldg(&A.payload[pb + (long long)r * G.K]);
-                    if (MODE == BWD_GRADIENT) Pv = make_float4(Pv.z, Pv.w, 0.f, 0.f);
+                const int p = ip.axis ? iy : ix;
+                const int q = ip.axis ? ix : iy;
+                const float pf = (float)p;
+                const float fq = __fmaf_rn(pf, ip.bq, ip.aq);
+                const float jq = floorf(fq);
+                const float aq = fq - jq;
+                float wq;
+                if (jq == (float)q) wq = 1.f - aq;
+                else if (jq == (float)(q - 1)) wq = aq;
+                else continue;
+                if (wq == 0.f) continue;
+                const float tp = ray_t(ip, pf);  // ray parameter at plane p
+                int r0 = 0, r1 = G.R - 1;
+                if (G.R > 1) {
+                    // fz(r) = sigma_z + t (omega0 + r domega): rows whose sample can
+                    // land in [z0 - 1, z0 + SLAB).  Solved in FP32 with the fast
+                    // reciprocal (within ~1e-6 rows of the rounded samples); a
+                    // 0.02-row margin keeps every contributing row, and the exact
+                    // per-row slot test below decides.
+                    const float slope = tp * G.domega;
+                    if (fabsf(slope) > 1e-20f) {
+                        const float inv = __fdividef(1.f, slope);
+                        const float base = fmaf(tp, G.omega0, sz);
+                        const float ra = (zlo - base) * inv, rb = (zhi - base) * inv;
+                        const float lo = fminf(fmaxf(fminf(ra, rb), -4.f), (float)G.R + 4.f);
+                        const float hi = fminf(fmaxf(fmaxf(ra, rb), -4.f), (float)G.R + 4.f);
+                        r0 = max(0, (int)floorf(lo - 0.02f));
+                        r1 = min(G.R - 1, (int)ceilf(hi + 0.02f));
+                    }
                 }
-                const float fz = row_fz(sz, row_omega(G, r), tp);
-                const float jz = floorf(fz);
-                const float az = fz - jz;
-                const int sl = (int)jz - z0;
-                // the payload carries h's row length factor already (folded by
-                // the forward kernel); A^T of caller data applies it here
-                const float w = MODE == BWD_ADJOINT ? Lq * __ldg(&G.row[r]).y : Lq;
-                const float w1 = w * az, w0 = w - w1;
-                if (!PEND) {
-                    if (sl >= 0 && sl < SLAB) {
-                        float4& a = acc[sl * NT + tid];
-                        a.x = fmaf(w0, Pv.x, a.x);
-                        a.y = fmaf(w0, Pv.y, a.y);
-                        if (FOUR) {
-                            a.z = fmaf(w0, Pv.z, a.z);
-                            a.w = fmaf(w0, Pv.w, a.w);
-                        }
-                    }
-                    if (sl >= -1 && sl + 1 < SLAB) {
-                        float4& a = acc[(sl + 1) * NT + tid];
-                        a.x = fmaf(w1, Pv.x, a.x);
-                        a.y = fmaf(w1, Pv.y, a.y);
-                        if (FOUR) {
-                            a.z = fmaf(w1, Pv.z, a.z);
-                            a.w = fmaf(w1, Pv.w, a.w);
-                        }
-                    }
+                const float Lq = ip.Lxy * wq;
+                // two or more rows fall in one slice, so consecutive rows add to the
+                // same slot pair: keep it in registers (plo: slot ls, phi: slot
+                // ls + 1) and write shared memory when the slot moves on
+                float4 plo = make_float4(0.f, 0.f, 0.f, 0.f), phi = plo;
+                int ls = -1000;
+                // ray data [V][R][K]: a warp's columns read neighbouring channels of a row
+                const long long pb = vbase * G.R + k;
+                if (!DEAM_IN_BOUNDS(G, pb + (long long)r1 * G.K < (long long)G.V * G.R * G.K, SITE_BWD_RAY,
+                                    pb + (long long)r1 * G.K))
                     continue;
-                }
-                if (sl != ls) {   // slots rise with r: flush the slot that is complete
-                    pend_flush<FOUR, SLAB, NT>(acc, ls, tid, plo);
-                    if (sl == ls + 1) {
-                        plo = phi;
+    #pragma unroll 4
+                for (int r = r0; r <= r1; ++r) {
+                    float4 Pv;
+                    if (MODE == BWD_ADJOINT) {
+                        const float2 t = __ldg(&A.rays2[pb + (long long)r * G.K]);
+                        Pv = make_float4(t.x, t.y, 0.f, 0.f);
                     } else {
-                        pend_flush<FOUR, SLAB, NT>(acc, ls + 1, tid, phi);
-                        plo = make_float4(0.f, 0.f, 0.f, 0.f);
+                        Pv = __ldg(&A.payload[pb + (long long)r * G.K]);
+                        if (MODE == BWD_GRADIENT) Pv = make_float4(Pv.z, Pv.w, 0.f, 0.f);
                     }
-                    phi = make_float4(0.f, 0.f, 0.f, 0.f);
-                    ls = sl;
+                    const float fz = row_fz(sz, row_omega(G, r), tp);
+                    const float jz = floorf(fz);
+                    const float az = fz - jz;
+                    const int sl = (int)jz - z0;
+                    // the payload carries h's row length factor already (folded by
+                    // the forward kernel); A^T of caller data applies it here
+                    const float w = MODE == BWD_ADJOINT ? Lq * __ldg(&G.row[r]).y : Lq;
+                    const float w1 = w * az, w0 = w - w1;
+                    if (sl != ls) {   // slots rise with r: flush the slot that is complete
+                        pend_flush<FOUR, SLAB, NT>(acc, ls, tid, plo);
+                        if (sl == ls + 1) {
+                            plo = phi;
+                        } else {
+                            pend_flush<FOUR, SLAB, NT>(acc, ls + 1, tid, phi);
+                            plo = make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
+                        phi = make_float4(0.f, 0.f, 0.f, 0.f);
+                        ls = sl;
+                    }
+                    plo.x = fmaf(w0, Pv.x, plo.x);
+                    plo.y = fmaf(w0, Pv.y, plo.y);
+                    phi.x = fmaf(w1, Pv.x, phi.x);
+                    phi.y = fmaf(w1, Pv.y, phi.y);
+                    if (FOUR) {
+                        plo.z = fmaf(w0, Pv.z, plo.z);
+                        plo.w = fmaf(w0, Pv.w, plo.w);
+                        phi.z = fmaf(w1, Pv.z, phi.z);
+                        phi.w = fmaf(w1, Pv.w, phi.w);
+                    }
                 }
-                plo.x = fmaf(w0, Pv.x, plo.x);
-                plo.y = fmaf(w0, Pv.y, plo.y);
-                phi.x = fmaf(w1, Pv.x, phi.x);
-                phi.y = fmaf(w1, Pv.y, phi.y);
-                if (FOUR) {
-                    plo.z = fmaf(w0, Pv.z, plo.z);
-                    plo.w = fmaf(w0, Pv.w, plo.w);
-                    phi.z = fmaf(w1, Pv.z, phi.z);
-                    phi.w = fmaf(w1, Pv.w, phi.w);
-                }
-            }
-            if (PEND) {
                 pend_flush<FOUR, SLAB, NT>(acc, ls, tid, plo);
                 pend_flush<FOUR, SLAB, NT>(acc, ls + 1, tid, phi);
             }
