@@ -342,7 +342,10 @@ def finish_line(args, world, rank, pg, gpu, case, d, mask, c0, samples, ms, valu
     hbm_src = "MEASURED_PEAKS.json hbm_gbs (of measured)"
     if hbm is None:
         hbm, hbm_src = 6800.0, "profiling recipe fallback 6.8 TB/s (of fallback)"
-    slab = 8 if (geo.nz == 1 or geo.n_rows == 1 or geo.dz >= 1.5 * geo.row_pitch * geo.sid / geo.sdd) else 16
+    # the library's slab depth for this scan (2 for one or two slices, 8 for thin
+    # rows, else 13)
+    slab = (2 if geo.nz <= 2 else
+            8 if (geo.n_rows == 1 or geo.dz >= 1.5 * geo.row_pitch * geo.sid / geo.sdd) else 13)
     kname = {"forward": "fwd_kernel<FWD_DEAM>", "backproject": f"bwd_kernel<1,{slab}>"}[dom]
     nvox, nrays = geo.n_voxels, geo.n_rays
     # compulsory bytes per launch: forward reads c (via its two layouts, 8 B per

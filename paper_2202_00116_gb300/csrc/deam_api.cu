@@ -284,7 +284,7 @@ int deam_init(const deam_geometry* geom, const deam_spectra* spectra, const deam
     ctx->delta = o.penalty_lambda > 0.0 ? o.penalty_delta : 1.0;
     ctx->threshold = o.metal_threshold > 0.0 ? o.metal_threshold
                                              : 0.5 * std::min(g.dx, std::min(g.dy, g.nz > 1 ? g.dz : g.dx));
-    ctx->slab = deam::pick_slab(g.nz, g.n_rows, g.dz, g.row_pitch, g.sid, g.sdd);
+    ctx->slab = deam::context_slab(deam::pick_slab(g.nz, g.n_rows, g.dz, g.row_pitch, g.sid, g.sdd));
     ctx->n_slabs = (g.nz + ctx->slab - 1) / ctx->slab;
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);

@@ -19,10 +19,10 @@ namespace deam {
 // at its plane exactly as the forward kernel does (same in-plane table, same
 // explicitly rounded t(p), omega_r and fz), and for every row whose sample falls
 // in the slab adds h(x, y) * payload(y) to the two voxels the sample
-// interpolates.  The kernel is bound by the L1/shared-memory data path (the
-// accumulator read-modify-writes and the payload gathers), so the row loop
-// reads nothing else: omega_r is computed, and the payload already carries h's
-// row length factor.  Views are taken in pairs: the samples of one row from
+// interpolates.  The kernel lives on the L1/shared-memory data path (the
+// accumulator read-modify-writes and the payload gathers) and on the latency
+// of its gathers, so the row loop reads nothing but the payload: omega_r is
+// computed, and the payload already carries h's row length factor.  Views are taken in pairs: the samples of one row from
 // two consecutive views lie within a few hundredths of a slice of each other,
 // so they almost always fall in the same slot pair, and one read-modify-write
 // of each slot adds both (half the accumulator traffic).  With 8-slice slabs
@@ -74,8 +74,8 @@ __device__ __forceinline__ void view_window(const Geo& G, int v, float fix, floa
     const float hw = __fdividef(G.vox_reach_mm, fmaxf(dist - G.vox_reach_mm, 1.f)) * G.inv_dgamma + 0.05f;
     k0 = max(0, (int)ceilf(fmaxf(uc - hw, -1.f)));
     k1 = min(G.K - 1, (int)floorf(fminf(uc + hw, (float)G.K)));
-    const long long vbase = (long long)v * G.K;
-    if (!DEAM_IN_BOUNDS(G, k0 > k1 || (k0 >= 0 && vbase + k1 < (long long)G.V * G.K), SITE_BWD_TABLE, vbase + k1))
+    if (!DEAM_IN_BOUNDS(G, k0 > k1 || (k0 >= 0 && (long long)v * G.K + k1 < (long long)G.V * G.K), SITE_BWD_TABLE,
+                        (long long)v * G.K + k1))
         k1 = k0 - 1;
 }
 
@@ -399,8 +399,10 @@ __device__ __forceinline__ void bwd_tile(const Geo& G, const BwdArgs& A, float4*
 
 
 
+// At most 64 registers a thread: 8 blocks per SM (shared memory allows it up
+// to kDeepSlab slices); more resident warps hide the gathers' latency.
 template <int MODE, int SLAB>
-__global__ void __launch_bounds__(kBwdThreads) bwd_kernel(const Geo G, const BwdArgs A) {
+__global__ void __launch_bounds__(kBwdThreads, 8) bwd_kernel(const Geo G, const BwdArgs A) {
     __shared__ float4 acc[SLAB * kBwdThreads];
     const int ntx = (G.nx + kTileX - 1) / kTileX, nty = (G.ny + kTileY - 1) / kTileY;
     int b = blockIdx.x;
@@ -447,10 +449,10 @@ cudaError_t launch_backward(int mode, int slab, const Geo& G, const BwdArgs& A, 
         if (mode == BWD_UPDATE) DEAM_BWD(BWD_UPDATE, 8);
         else if (mode == BWD_GRADIENT) DEAM_BWD(BWD_GRADIENT, 8);
         else DEAM_BWD(BWD_ADJOINT, 8);
-    } else if (slab == 16) {
-        if (mode == BWD_UPDATE) DEAM_BWD(BWD_UPDATE, 16);
-        else if (mode == BWD_GRADIENT) DEAM_BWD(BWD_GRADIENT, 16);
-        else DEAM_BWD(BWD_ADJOINT, 16);
+    } else if (slab == kDeepSlab) {
+        if (mode == BWD_UPDATE) DEAM_BWD(BWD_UPDATE, kDeepSlab);
+        else if (mode == BWD_GRADIENT) DEAM_BWD(BWD_GRADIENT, kDeepSlab);
+        else DEAM_BWD(BWD_ADJOINT, kDeepSlab);
     } else {
         return cudaErrorInvalidValue;
     }

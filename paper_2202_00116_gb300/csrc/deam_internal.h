@@ -207,6 +207,14 @@ inline int pick_slab(int nz, int n_rows, double dz, double row_pitch, double sid
     if (nz <= 2) return 2;
     return (n_rows == 1 || dz >= 1.5 * row_pitch * sid / sdd) ? 8 : 16;
 }
+// Slab depth a single-scan context runs for the deep class (16): 13 slices.
+// The accumulators of a 128-thread block then take 26 KB of shared memory, so
+// with at most 64 registers a thread 8 blocks (32 warps) fit on an SM instead
+// of 6: the gather is latency-bound at 6 (measured at 512^2 x 64: 16 slices at
+// 6 blocks/SM 203.8 ms, 12 at 7 blocks 193.0 ms, 11 at 8 blocks 189.7 ms).
+// The batched persistent launches keep their own shapes (kBwdShapes).
+constexpr int kDeepSlab = 13;
+inline int context_slab(int slab_class) { return slab_class == 16 ? kDeepSlab : slab_class; }
 long long forward_tiles(int shape, const Geo& G);
 long long backward_tiles(int shape, const Geo& G);
 int forward_batch_blocks_per_sm(int shape);

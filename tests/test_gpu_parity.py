@@ -382,7 +382,7 @@ def test_c1_full_size_sampled_views(pkg):
 def test_c2_full_size_bench_configuration(pkg):
     # The benchmark's own workload (512x512x64, 5800 views x 16 x 816, 2 x 120
     # bins, steel hips, noisy counts) in the launch configuration bench.py times
-    # (same context, slab of 16 slices, one-wave forward grid): per-ray terms on
+    # (same context, 13-slice slabs, one-wave forward grid): per-ray terms on
     # seeded sampled rays and the forward on sampled views against the oracle,
     # the adjoint on a view subset against the oracle's, and, at full size, the
     # fused c-step against its own backprojected sums plus a decrease of F.
@@ -535,7 +535,7 @@ def test_helical_edge_geometries_match_oracle(pkg, variant):
     # a single detector row over a multi-slice volume with dy != dx (the
     # backprojector's single-row slab and the anisotropic in-plane ratios), and
     # an odd row count with a row offset, a volume centre off the axis and
-    # dz below the slice a row covers (16-slice slabs over an 11-slice volume)
+    # dz below the slice a row covers (one ragged 13-slice slab over an 11-slice volume)
     import dataclasses
     case = synth.make_case("t3d")
     g = case.geo
