@@ -47,10 +47,10 @@ L1_BYTES_PER_SAMPLE = 32.0
 # in profiles/); traffic grows with the views, so it is scaled by the sample
 # count of the measured launch.  Kernels without a capture of their current
 # build are absent (traffic null).
-DRAM_BYTES_PER_SAMPLE = {"bwd_kernel<1,16>": (2.9376e9 + 0.1232e9) / 6.4845e9,
-                         "fwd_kernel<FWD_DEAM>": (1.9210e9 + 0.2395e9) / 6.4845e9}
+DRAM_BYTES_PER_SAMPLE = {"bwd_kernel<1,13>": (2.9176e9 + 0.1196e9) / 6.4845e9,
+                         "fwd_kernel<FWD_DEAM>": (1.9193e9 + 0.2392e9) / 6.4845e9}
 # L1/TEX utilisation of the same kernels in those captures.
-L1_BUSY = {"bwd_kernel<1,16>": 0.947, "fwd_kernel<FWD_DEAM>": 0.673}
+L1_BUSY = {"bwd_kernel<1,13>": 0.828, "fwd_kernel<FWD_DEAM>": 0.682}
 
 
 def _peaks():
