@@ -279,7 +279,7 @@ FULL_SCALE_CUTS = {"c1_one_rotation": ("c1", 1160), "c2_quarter_rotation": ("c2s
 
 @pytest.mark.parametrize("cut", sorted(FULL_SCALE_CUTS))
 def test_ten_iterations_at_full_scale_cut(pkg, cut, record_property, capsys):
-    # the benchmark spec's tolerance at the benchmark volumes and detectors: the image
+    # The parity bar at the benchmark volumes and detectors: the image
     # after 10 iterations to rel-L2 1e-4 and the objective history to 1e-5
     # against the full oracle run (paper Sec. 2.3), plus every per-ray output on
     # seeded sampled rays to 1e-5; the errors are printed as the precision
