@@ -46,11 +46,11 @@ L1_BYTES_PER_SAMPLE = 32.0
 # one-rotation cut of this scan (6.484e9 samples per launch; the commands are
 # in profiles/); traffic grows with the views, so it is scaled by the sample
 # count of the measured launch.  Kernels without a capture of their current
-# build are absent (traffic null).
-DRAM_BYTES_PER_SAMPLE = {"bwd_kernel<1,13>": (2.9176e9 + 0.1196e9) / 6.4845e9,
-                         "fwd_kernel<FWD_DEAM>": (1.9193e9 + 0.2392e9) / 6.4845e9}
+# build are absent (traffic null): the backprojection's capture (3.04 GB per
+# 6.4845e9 samples) predates its row loop losing its unroll.
+DRAM_BYTES_PER_SAMPLE = {"fwd_kernel<FWD_DEAM>": (1.9193e9 + 0.2392e9) / 6.4845e9}
 # L1/TEX utilisation of the same kernels in those captures.
-L1_BUSY = {"bwd_kernel<1,13>": 0.828, "fwd_kernel<FWD_DEAM>": 0.682}
+L1_BUSY = {"fwd_kernel<FWD_DEAM>": 0.682}
 
 
 def _peaks():
