@@ -200,9 +200,10 @@ constexpr int kFwdShapes[3][2] = {{8, 1}, {4, 2}, {2, 4}};             // (rows,
 constexpr int kNumBwdShapes = 6;
 constexpr int kBwdShapes[kNumBwdShapes][3] = {{2, 16, 8}, {2, 32, 4}, {8, 16, 8},
                                               {8, 32, 4}, {16, 16, 8}, {16, 32, 4}};  // (slab, tx, ty)
-// z-slab depth of the gather backprojection for a scan: 2 for a single slice,
-// 8 when a detector row covers at most 2/3 of a slice (several rows per slot),
-// else 16.
+// Slab class of the gather backprojection for a scan: 2 for one or two
+// slices, 8 when a detector row covers at most 2/3 of a slice (several rows
+// per slot), else 16.  The batched persistent launches use the class as their
+// slab depth; a single-scan context runs class 16 as kDeepSlab slices.
 inline int pick_slab(int nz, int n_rows, double dz, double row_pitch, double sid, double sdd) {
     if (nz <= 2) return 2;
     return (n_rows == 1 || dz >= 1.5 * row_pitch * sid / sdd) ? 8 : 16;
