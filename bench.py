@@ -117,6 +117,15 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def workload_config(args, case, world):
+    """The `config` object of both arms' JSON lines (the same keys and values,
+    so the two lines name one workload)."""
+    n = case.geo.n_rays
+    return {"workload": WORKLOAD, "case": args.config, "parallelism": f"replicas x{world}",
+            "l2": (f"working set larger than L2 (payload {16 * n / 1e9:.2f} GB + data {8 * n / 1e9:.2f} GB "
+                   f"per iteration)")}
+
+
 def build_workload(name, device):
     import torch
 
@@ -222,7 +231,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec_per_step,
             "sample_fraction_per_step": frac,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "case": args.config},
+            "data": "synthetic", "config": workload_config(args, case, world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -379,8 +388,7 @@ def finish_line(args, world, rank, pg, gpu, case, d, mask, c0, samples, ms, valu
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded phantom, analytic polyenergetic projections, Poisson + Gaussian noise)",
-            "config": {"workload": WORKLOAD, "case": args.config, "parallelism": f"replicas x{world}",
-                       "l2": "working set larger than L2 (payload 1.2 GB + data 0.6 GB per iteration)"},
+            "config": workload_config(args, case, world),
             "ray_samples_per_projection": samples,
             "ray_samples_per_s": samples * value,
             "stage_ms": {s: avg[s] for s in stages},

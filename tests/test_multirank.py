@@ -112,3 +112,9 @@ def test_reference_arm_under_torchrun(oracle_lib):
     line = json.loads(lines[0])
     assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "it/s"
     assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
+    # the same config object as the GPU arm's line (bench.workload_config)
+    sys.path.insert(0, ROOT)
+    import bench
+    import synth
+    args = type("A", (), {"config": "t2d"})()
+    assert line["config"] == bench.workload_config(args, synth.make_case("t2d"), 2)
